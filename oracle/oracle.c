@@ -1,0 +1,466 @@
+/*
+ * oracle.c -- plain, slow CPU reference for maximal clique enumeration.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header,
+ * table or helper with the CUDA library; the two meet only in the seeded
+ * input generators.
+ *
+ * Graphs arrive in CSR form: vertex v's neighbours are
+ * adj[off[v] .. off[v+1]), sorted ascending, symmetric, no self-loops,
+ * vertices 0..n-1 (the paper's Section 2 numbers them 1..n).
+ *
+ * Two enumerators live here.
+ *
+ *  1. oracle_tomita: the Bron-Kerbosch recursion with pivoting (Alg. 2,
+ *     Section 3.2) over sorted vertex arrays, with the Tomita pivot
+ *     u = argmax_{u in P u X} |P n N(u)| (Section 3.2), ties to the smallest
+ *     label.  It defines the *result*: the set of maximal cliques, which does
+ *     not depend on ordering or pivot rule.
+ *
+ *  2. oracle_ordered: the paper's own search tree, so that search-node
+ *     counts can be compared exactly.  It computes the maximum-degree-first
+ *     ordering (Section 4.2), renumbers the graph by position (Section 4.2,
+ *     "How we use the vertex ordering") and runs BKPivotOrdered with
+ *     ChoosePivotOrdered (Alg. 4).  Pivot modes (Section 4.3):
+ *       0 GreedyBB    p = first vertex of X in the order, else first of P;
+ *       1 GreedyBBTX  p = argmax_{u in X} |P n N(u)|, else first of P;
+ *       2 TomitaBB    p = argmax_{u in P u X} |P n N(u)|;
+ *     argmax ties go to the vertex earliest in the order (Section 4.3).
+ *     Its sets are sorted arrays of positions, so "first in the order" is
+ *     element 0 -- no bitsets.
+ *
+ * Outputs shared by both (all counters modulo 2^64):
+ *   count      number of maximal cliques
+ *   hist[k]    number of maximal cliques with k vertices, k = 0..n
+ *   hash       sum over cliques K of h(K), where
+ *                S(K) = sum_{c in K} mix64(c + 1),  h(K) = mix64(S(K) ^ mix64(|K|))
+ *              with c the original 0-based label and mix64 the SplitMix64
+ *              finaliser (Steele, Lea, Flood, OOPSLA 2014).  h depends only on
+ *              the set K, so the total equals a hash of the sorted cliques.
+ *   nodes      invocations of the recursive procedure, root and leaves included
+ *   internal   invocations with P non-empty
+ *   dead_ends  invocations with P empty and X non-empty
+ *   listing    optional: each clique as [k, c_1, ..., c_k] (original labels,
+ *              ascending) appended to a flat array.
+ *
+ * n = 0 follows the BK definition: P = X = {} at the root, so R = {} is
+ * reported once (hist[0] = 1).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* SplitMix64 output function. */
+static uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t oracle_mix64(uint64_t z) { return mix64(z); }
+
+/* h(K) from the 0-based labels of K, in any order. */
+uint64_t oracle_clique_hash(const uint32_t *labels, uint32_t k)
+{
+    uint64_t s = 0;
+    for (uint32_t i = 0; i < k; ++i)
+        s += mix64((uint64_t)labels[i] + 1);
+    return mix64(s ^ mix64((uint64_t)k));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sorted-array set operations.                                              */
+
+/* out = a n b; returns |out|.  out may not alias a or b. */
+static uint32_t set_and(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb, uint32_t *out)
+{
+    uint32_t i = 0, j = 0, k = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j]) ++i;
+        else if (a[i] > b[j]) ++j;
+        else { out[k++] = a[i]; ++i; ++j; }
+    }
+    return k;
+}
+
+/* |a n b| */
+static uint32_t set_and_count(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb)
+{
+    uint32_t i = 0, j = 0, k = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j]) ++i;
+        else if (a[i] > b[j]) ++j;
+        else { ++k; ++i; ++j; }
+    }
+    return k;
+}
+
+/* out = a \ b; returns |out|. */
+static uint32_t set_minus(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb, uint32_t *out)
+{
+    uint32_t i = 0, j = 0, k = 0;
+    while (i < na) {
+        if (j < nb && b[j] < a[i]) { ++j; continue; }
+        if (j < nb && b[j] == a[i]) { ++i; ++j; continue; }
+        out[k++] = a[i++];
+    }
+    return k;
+}
+
+/* Remove x from sorted a (present); returns new size. */
+static uint32_t set_erase(uint32_t *a, uint32_t na, uint32_t x)
+{
+    uint32_t i = 0;
+    while (i < na && a[i] != x) ++i;
+    if (i < na) {
+        memmove(a + i, a + i + 1, (size_t)(na - i - 1) * sizeof(uint32_t));
+        return na - 1;
+    }
+    return na;
+}
+
+/* Insert x into sorted a (absent); returns new size. */
+static uint32_t set_insert(uint32_t *a, uint32_t na, uint32_t x)
+{
+    uint32_t i = 0;
+    while (i < na && a[i] < x) ++i;
+    memmove(a + i + 1, a + i, (size_t)(na - i) * sizeof(uint32_t));
+    a[i] = x;
+    return na + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shared bookkeeping for one enumeration.                                   */
+
+typedef struct {
+    uint32_t n;
+    const uint32_t *off, *adj;      /* neighbourhoods used by the recursion  */
+    const uint32_t *label;          /* recursion vertex -> original label    */
+    uint64_t count, nodes, internal, dead_ends, hash;
+    uint64_t *hist;                 /* n + 1 entries                         */
+    uint32_t *list;                 /* optional listing, may be NULL         */
+    uint64_t list_cap, list_used;
+    uint32_t *R;                    /* current clique (recursion vertices)   */
+    uint32_t *tmp;                  /* n scratch words                       */
+    uint32_t **lvl;                 /* per-depth buffers: P', X', L (3n)     */
+    uint32_t depth_alloc;
+    int mode;                       /* pivot rule of oracle_ordered          */
+    int32_t *trace;                 /* optional: first internal nodes        */
+    uint64_t trace_cap, trace_used;
+    int oom;
+} run_t;
+
+static uint32_t *level_buf(run_t *r, uint32_t d)
+{
+    if (d >= r->depth_alloc) {
+        uint32_t na = r->depth_alloc ? r->depth_alloc * 2 : 16;
+        while (na <= d) na *= 2;
+        uint32_t **nl = (uint32_t **)realloc(r->lvl, (size_t)na * sizeof(uint32_t *));
+        if (!nl) { r->oom = 1; return NULL; }
+        for (uint32_t i = r->depth_alloc; i < na; ++i) nl[i] = NULL;
+        r->lvl = nl;
+        r->depth_alloc = na;
+    }
+    if (!r->lvl[d]) {
+        r->lvl[d] = (uint32_t *)malloc((size_t)3 * (r->n + 1) * sizeof(uint32_t));
+        if (!r->lvl[d]) { r->oom = 1; return NULL; }
+    }
+    return r->lvl[d];
+}
+
+static void report(run_t *r, uint32_t rn)
+{
+    r->count++;
+    r->hist[rn]++;
+    uint64_t s = 0;
+    for (uint32_t i = 0; i < rn; ++i) {
+        r->tmp[i] = r->label[r->R[i]];
+        s += mix64((uint64_t)r->tmp[i] + 1);
+    }
+    r->hash += mix64(s ^ mix64((uint64_t)rn));
+    if (r->list) {
+        /* insertion sort: cliques are small */
+        for (uint32_t i = 1; i < rn; ++i) {
+            uint32_t x = r->tmp[i], j = i;
+            while (j > 0 && r->tmp[j - 1] > x) { r->tmp[j] = r->tmp[j - 1]; --j; }
+            r->tmp[j] = x;
+        }
+        if (r->list_used + rn + 1 <= r->list_cap) {
+            r->list[r->list_used] = rn;
+            memcpy(r->list + r->list_used + 1, r->tmp, (size_t)rn * sizeof(uint32_t));
+        }
+        r->list_used += rn + 1;
+    }
+}
+
+static void record_trace(run_t *r, uint32_t rn, uint32_t p, const uint32_t *L, uint32_t nl)
+{
+    /* record: [depth, pivot label, |L|, L labels...] */
+    if (!r->trace) return;
+    if (r->trace_used + 3 + nl > r->trace_cap) return;
+    int32_t *t = r->trace + r->trace_used;
+    t[0] = (int32_t)rn;
+    t[1] = (int32_t)r->label[p];
+    t[2] = (int32_t)nl;
+    for (uint32_t i = 0; i < nl; ++i) t[3 + i] = (int32_t)r->label[L[i]];
+    r->trace_used += 3 + nl;
+}
+
+static const uint32_t *nbr(const run_t *r, uint32_t v, uint32_t *deg)
+{
+    *deg = r->off[v + 1] - r->off[v];
+    return r->adj + r->off[v];
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1. BKPivot with the Tomita pivot (Alg. 2).                                */
+
+static void bk_tomita(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t nx, uint32_t rn)
+{
+    if (r->oom) return;
+    r->nodes++;
+    if (np == 0 && nx == 0) { report(r, rn); return; }
+    if (np == 0) { r->dead_ends++; return; }
+    r->internal++;
+
+    /* pivot: scan P u X in ascending label order; strict '>' keeps the
+     * smallest label among ties */
+    uint32_t best_u = 0, best_c = 0;
+    int have = 0;
+    uint32_t i = 0, j = 0;
+    while (i < np || j < nx) {
+        uint32_t u;
+        if (j >= nx || (i < np && P[i] < X[j])) u = P[i++];
+        else u = X[j++];
+        uint32_t du;
+        const uint32_t *nu = nbr(r, u, &du);
+        uint32_t c = set_and_count(P, np, nu, du);
+        if (!have || c > best_c) { best_c = c; best_u = u; have = 1; }
+    }
+
+    uint32_t *buf = level_buf(r, rn);
+    if (!buf) return;
+    uint32_t *L = buf + 2 * (r->n + 1);
+    uint32_t dp;
+    const uint32_t *np_ = nbr(r, best_u, &dp);
+    uint32_t nl = set_minus(P, np, np_, dp, L);
+
+    for (uint32_t t = 0; t < nl; ++t) {
+        uint32_t v = L[t];
+        uint32_t dv;
+        const uint32_t *nv = nbr(r, v, &dv);
+        /* child buffers live one level down */
+        uint32_t *cb = level_buf(r, rn + 1);
+        if (!cb) return;
+        /* buf (level rn) holds this node's P' and X' scratch: reuse lvl[rn+1]
+         * for the child's own sets so the child can mutate them. */
+        uint32_t *cP = cb, *cX = cb + (r->n + 1);
+        uint32_t ncp = set_and(P, np, nv, dv, cP);
+        uint32_t ncx = set_and(X, nx, nv, dv, cX);
+        r->R[rn] = v;
+        bk_tomita(r, cP, ncp, cX, ncx, rn + 1);
+        np = set_erase(P, np, v);
+        nx = set_insert(X, nx, v);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2. BKPivotOrdered (Alg. 4) on the renumbered graph.                        */
+
+static void bk_ordered(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t nx, uint32_t rn)
+{
+    if (r->oom) return;
+    r->nodes++;
+    if (np == 0 && nx == 0) { report(r, rn); return; }
+    if (np == 0) { r->dead_ends++; return; }
+    r->internal++;
+
+    /* ChoosePivotOrdered.  Sets hold positions, so element 0 is the vertex
+     * earliest in the order; scanning ascending with strict '>' gives the
+     * earliest vertex among argmax ties. */
+    uint32_t p;
+    if (r->mode == 0) {
+        p = nx ? X[0] : P[0];
+    } else if (r->mode == 1) {
+        if (nx) {
+            uint32_t best_c = 0; p = X[0];
+            for (uint32_t i = 0; i < nx; ++i) {
+                uint32_t du; const uint32_t *nu = nbr(r, X[i], &du);
+                uint32_t c = set_and_count(P, np, nu, du);
+                if (i == 0 || c > best_c) { best_c = c; p = X[i]; }
+            }
+        } else {
+            p = P[0];
+        }
+    } else {
+        uint32_t best_c = 0; int have = 0; p = 0;
+        uint32_t i = 0, j = 0;
+        while (i < np || j < nx) {
+            uint32_t u;
+            if (j >= nx || (i < np && P[i] < X[j])) u = P[i++];
+            else u = X[j++];
+            uint32_t du; const uint32_t *nu = nbr(r, u, &du);
+            uint32_t c = set_and_count(P, np, nu, du);
+            if (!have || c > best_c) { best_c = c; p = u; have = 1; }
+        }
+    }
+
+    uint32_t *buf = level_buf(r, rn);
+    if (!buf) return;
+    uint32_t *L = buf + 2 * (r->n + 1);
+    uint32_t dp; const uint32_t *npv = nbr(r, p, &dp);
+    /* L = P \ N(p); p itself stays in L when p is in P (p is not in N(p)) */
+    uint32_t nl = set_minus(P, np, npv, dp, L);
+    record_trace(r, rn, p, L, nl);
+
+    /* branch on L in increasing position: v = argmin_{w in L} phi(w) */
+    for (uint32_t t = 0; t < nl; ++t) {
+        uint32_t v = L[t];
+        uint32_t dv; const uint32_t *nv = nbr(r, v, &dv);
+        uint32_t *cb = level_buf(r, rn + 1);
+        if (!cb) return;
+        uint32_t *cP = cb, *cX = cb + (r->n + 1);
+        uint32_t ncp = set_and(P, np, nv, dv, cP);
+        uint32_t ncx = set_and(X, nx, nv, dv, cX);
+        r->R[rn] = v;
+        bk_ordered(r, cP, ncp, cX, ncx, rn + 1);
+        np = set_erase(P, np, v);
+        nx = set_insert(X, nx, v);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Maximum-degree-first ordering (Section 4.2): v_1 has maximum degree in G,
+ * v_{i+1} has maximum degree in the subgraph induced by the vertices not yet
+ * placed.  Ties go to the smallest original label (the paper does not say). */
+
+void oracle_mdf_order(uint32_t n, const uint32_t *off, const uint32_t *adj, uint32_t *order)
+{
+    uint32_t *deg = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    unsigned char *placed = (unsigned char *)calloc(n ? n : 1, 1);
+    for (uint32_t v = 0; v < n; ++v) deg[v] = off[v + 1] - off[v];
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t best = 0; int have = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            if (placed[v]) continue;
+            if (!have || deg[v] > deg[best]) { best = v; have = 1; }
+        }
+        order[i] = best;
+        placed[best] = 1;
+        for (uint32_t e = off[best]; e < off[best + 1]; ++e)
+            if (!placed[adj[e]]) deg[adj[e]]--;
+    }
+    free(deg);
+    free(placed);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entry points.  stats[] receives {count, nodes, internal, dead_ends, hash}.
+ * Returns 0, or -2 when memory ran out. */
+
+static int run_init(run_t *r, uint32_t n, uint64_t *hist, uint32_t *list, uint64_t list_cap)
+{
+    memset(r, 0, sizeof(*r));
+    r->n = n;
+    r->hist = hist;
+    memset(hist, 0, (size_t)(n + 1) * sizeof(uint64_t));
+    r->list = list;
+    r->list_cap = list ? list_cap : 0;
+    r->R = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    r->tmp = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    return (r->R && r->tmp) ? 0 : -2;
+}
+
+static void run_free(run_t *r)
+{
+    for (uint32_t i = 0; i < r->depth_alloc; ++i) free(r->lvl[i]);
+    free(r->lvl);
+    free(r->R);
+    free(r->tmp);
+}
+
+static void run_stats(const run_t *r, uint64_t *stats, uint64_t *list_used)
+{
+    stats[0] = r->count;
+    stats[1] = r->nodes;
+    stats[2] = r->internal;
+    stats[3] = r->dead_ends;
+    stats[4] = r->hash;
+    if (list_used) *list_used = r->list_used;
+}
+
+int oracle_tomita(uint32_t n, const uint32_t *off, const uint32_t *adj,
+                  uint64_t *stats, uint64_t *hist,
+                  uint32_t *list, uint64_t list_cap, uint64_t *list_used)
+{
+    run_t r;
+    int rc = run_init(&r, n, hist, list, list_cap);
+    uint32_t *ident = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    uint32_t *X = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    if (rc || !ident || !P || !X) { rc = -2; goto done; }
+    for (uint32_t v = 0; v < n; ++v) { ident[v] = v; P[v] = v; }
+    r.off = off; r.adj = adj; r.label = ident;
+    bk_tomita(&r, P, n, X, 0, 0);
+    rc = r.oom ? -2 : 0;
+    run_stats(&r, stats, list_used);
+done:
+    free(ident); free(P); free(X);
+    run_free(&r);
+    return rc;
+}
+
+/* order: NULL -> maximum-degree-first; else order[i] = vertex at position i.
+ * order_out (optional) receives the order used. */
+int oracle_ordered(uint32_t n, const uint32_t *off, const uint32_t *adj,
+                   int mode, const uint32_t *order, uint32_t *order_out,
+                   uint64_t *stats, uint64_t *hist,
+                   uint32_t *list, uint64_t list_cap, uint64_t *list_used,
+                   int32_t *trace, uint64_t trace_cap, uint64_t *trace_used)
+{
+    run_t r;
+    int rc = run_init(&r, n, hist, list, list_cap);
+    size_t nn = (size_t)(n ? n : 1);
+    uint32_t *ord = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    uint32_t *pos = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    uint32_t *roff = (uint32_t *)malloc((nn + 1) * sizeof(uint32_t));
+    uint32_t m2 = n ? off[n] : 0;
+    uint32_t *radj = (uint32_t *)malloc((size_t)(m2 ? m2 : 1) * sizeof(uint32_t));
+    uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    uint32_t *X = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    if (rc || !ord || !pos || !roff || !radj || !P || !X) { rc = -2; goto done; }
+
+    if (order) memcpy(ord, order, (size_t)n * sizeof(uint32_t));
+    else oracle_mdf_order(n, off, adj, ord);
+    if (order_out) memcpy(order_out, ord, (size_t)n * sizeof(uint32_t));
+    for (uint32_t i = 0; i < n; ++i) pos[ord[i]] = i;
+
+    /* Renumber: position i is vertex ord[i]; its neighbours become positions,
+     * sorted, so the order is kept inside every set (Section 4.2). */
+    roff[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t v = ord[i], k = roff[i];
+        for (uint32_t e = off[v]; e < off[v + 1]; ++e) radj[k++] = pos[adj[e]];
+        roff[i + 1] = k;
+        /* insertion sort of the new row (plain and obviously correct) */
+        for (uint32_t a = roff[i] + 1; a < k; ++a) {
+            uint32_t x = radj[a], b = a;
+            while (b > roff[i] && radj[b - 1] > x) { radj[b] = radj[b - 1]; --b; }
+            radj[b] = x;
+        }
+    }
+
+    r.off = roff; r.adj = radj; r.label = ord; r.mode = mode;
+    r.trace = trace; r.trace_cap = trace ? trace_cap : 0;
+    for (uint32_t i = 0; i < n; ++i) P[i] = i;
+    bk_ordered(&r, P, n, X, 0, 0);
+    rc = r.oom ? -2 : 0;
+    run_stats(&r, stats, list_used);
+    if (trace_used) *trace_used = r.trace_used;
+done:
+    free(ord); free(pos); free(roff); free(radj); free(P); free(X);
+    run_free(&r);
+    return rc;
+}
