@@ -1,0 +1,239 @@
+/*
+ * mce.h -- C ABI of libmce, a GB300 (sm_103a) implementation of maximal
+ * clique enumeration by bit-parallel Bron-Kerbosch search with a static
+ * maximum-degree-first vertex order and greedy pivot selection
+ * (San Segundo, Artieda and Strash, "Efficiently Enumerating all Maximal
+ * Cliques with Bit-Parallelism": Alg. 4, Sections 4.1-4.3).
+ *
+ * Problem (Section 1, Section 2): given a simple undirected graph
+ * G = (V, E), V = {0, ..., n-1} (the paper numbers vertices from 1), report
+ * every maximal clique: a set K of pairwise adjacent vertices such that no
+ * vertex outside K is adjacent to all of K.  The library reports
+ *
+ *   count      |{maximal cliques}|
+ *   hist[k]    number of maximal cliques with k vertices, k = 0..n
+ *   hash       sum over cliques K of h(K) modulo 2^64, where
+ *                S(K) = sum_{c in K} mix64(c + 1) (c = original 0-based label),
+ *                h(K) = mix64(S(K) xor mix64(|K|)),
+ *              mix64 = the SplitMix64 finaliser (Steele, Lea and Flood,
+ *              OOPSLA 2014).  h depends only on the vertex set, so the total
+ *              is an order-independent hash of the sorted cliques.
+ *   nodes      search-tree nodes: invocations of BKPivotOrdered (Alg. 4),
+ *              the root and the leaves included;
+ *   internal   nodes with P non-empty;  dead_ends: P empty, X non-empty.
+ *
+ * n = 0 follows the Bron-Kerbosch definition (Alg. 1): the empty set is the
+ * one maximal clique (hist[0] = 1).  Isolated vertices are maximal cliques of
+ * size 1.
+ *
+ * Adjacency bitset layout (used by every call that takes "rows"): row v is
+ * words_per_row consecutive uint32 words; vertex u is bit (u % 32) of word
+ * (u / 32).  words_per_row >= ceil(n / 32).  A valid bitset is symmetric,
+ * has a zero diagonal and zero bits at positions >= n.
+ *
+ * Return codes: every function returns one of the MCE_* codes below.
+ * Device-level calls ("_device" suffix or taking d_* pointers) are
+ * stream-ordered: they enqueue work on `stream` (a cudaStream_t; NULL =
+ * legacy default stream) and return MCE_OK once it is enqueued; errors found
+ * while the kernels run are written to d_out[MCE_OUT_STATUS].  Host-level
+ * calls copy their inputs during the call (the caller keeps ownership) and
+ * return after the result is on the host.
+ *
+ * Thread safety: handles (mce_ctx, mce_graph) must not be used from two host
+ * threads at once.  Distinct contexts are independent.
+ */
+#ifndef MCE_H
+#define MCE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- */
+/* Return codes                                                              */
+
+#define MCE_OK         0
+#define MCE_PENDING    1   /* request not finished yet (mce_poll)            */
+#define MCE_EINVAL    -1   /* bad argument: self-loop, id >= n, asymmetric or
+                              padded-bit-set bitset, n > MCE_NMAX, NULL ptr  */
+#define MCE_ENOMEM    -2   /* device or host allocation failed / too small   */
+#define MCE_ECUDA     -3   /* a CUDA call failed                             */
+#define MCE_ETRUNC    -4   /* listing or histogram buffer too small; the
+                              *_needed fields are filled, counters are valid */
+#define MCE_ETIMEOUT  -5   /* a bounded wait (device or host) gave up        */
+#define MCE_EOVERFLOW -6   /* the device work queue overflowed               */
+#define MCE_ENOTIMPL  -7   /* option combination not implemented             */
+
+#define MCE_NMAX 4096u     /* largest supported number of vertices           */
+
+/* ----------------------------------------------------------------------- */
+/* Options                                                                   */
+
+/* Pivot rules (Section 4.3).  GREEDY: first vertex of X in the order, else
+ * first of P (GreedyBB, the paper's main variant).  GREEDY_TX: the vertex of
+ * X maximising |P n N(u)|, else first of P (GreedyBBTX).  TOMITA: the vertex
+ * of P u X maximising |P n N(u)| (TomitaBB).  Ties go to the vertex earliest
+ * in the order. */
+#define MCE_PIVOT_GREEDY     0u
+#define MCE_PIVOT_GREEDY_TX  1u
+#define MCE_PIVOT_TOMITA     2u
+
+/* flags */
+#define MCE_ORDER_IDENTITY   0x1u  /* skip the maximum-degree-first ordering
+                                      (Section 4.2): the input order is the
+                                      search order                            */
+#define MCE_LIST             0x2u  /* also return the cliques (host API only) */
+#define MCE_LIST_SORTED      0x4u  /* sort each clique and the listing        */
+
+typedef struct {
+    uint32_t pivot_mode;        /* MCE_PIVOT_*                                */
+    uint32_t flags;             /* MCE_ORDER_IDENTITY | MCE_LIST | ...        */
+    uint32_t lanes_per_subtree; /* lanes of a warp that share one search
+                                   subtree: 1,2,4,8,16,32; 0 = autotuned       */
+    uint32_t words_per_lane;    /* 32-bit words of each set a lane holds:
+                                   1,2,4; 0 = autotuned                       */
+    uint32_t blocks;            /* persistent grid size; 0 = one wave         */
+    uint32_t threads_per_block; /* 0 = autotuned                              */
+    uint64_t timeout_ns;        /* device-side wait budget: a search whose
+                                   idle warps see no progress for this long
+                                   stops with MCE_ETIMEOUT; 0 = 60 s          */
+    uint32_t stack_levels;      /* explicit-stack levels per subtree before
+                                   frames spill to the device work queue,
+                                   1..64; 0 = 64                              */
+    uint32_t _reserved;
+} mce_options;
+
+/* Layout of the device result array d_out (uint64 words, zeroed and filled
+ * by the device calls).  hist[k] is at d_out[MCE_OUT_HIST + k]. */
+#define MCE_OUT_COUNT      0
+#define MCE_OUT_NODES      1
+#define MCE_OUT_INTERNAL   2
+#define MCE_OUT_DEAD_ENDS  3
+#define MCE_OUT_HASH       4
+#define MCE_OUT_STATUS     5   /* 0 or a negative MCE_* code (as int64)      */
+#define MCE_OUT_MAX_SIZE   6   /* size of the largest maximal clique         */
+#define MCE_OUT_DONATIONS  7   /* work frames handed between warps           */
+#define MCE_OUT_HIST       16
+#define MCE_OUT_WORDS(n)   (MCE_OUT_HIST + (uint64_t)(n) + 1)
+
+/* ----------------------------------------------------------------------- */
+/* Device-level, stream-ordered calls.  All d_* pointers are device memory
+ * owned by the caller; nothing is allocated.  They are the steps of the
+ * search path and may be called one by one or through
+ * mce_enumerate_device. */
+
+/* Step "input canonicalisation" from an edge list (Section 2: simple
+ * undirected graph).  d_uv holds m pairs (u, v) as 2*m uint32, host order
+ * irrelevant, duplicates and both orientations allowed.  Writes the
+ * symmetric bitset d_rows (n * words_per_row words; it is cleared first).
+ * A self-loop or an id >= n sets d_out[MCE_OUT_STATUS] = MCE_EINVAL (d_out
+ * must hold MCE_OUT_WORDS(n) words; only the status word is touched). */
+int mce_edges_to_rows(uint32_t n, uint64_t m, const uint32_t *d_uv,
+                      uint32_t words_per_row, uint32_t *d_rows,
+                      uint64_t *d_out, void *stream);
+
+/* Step "input canonicalisation" for a bitset: checks symmetry, zero
+ * diagonal and zero padding bits; on failure sets d_out[MCE_OUT_STATUS] =
+ * MCE_EINVAL. */
+int mce_validate_rows(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+                      uint64_t *d_out, void *stream);
+
+/* Maximum-degree-first ordering (Section 4.2): d_order[0] is a vertex of
+ * maximum degree in G, d_order[i] a vertex of maximum degree in the graph
+ * induced by the vertices not yet placed; ties go to the smallest label.
+ * d_order receives n uint32. */
+int mce_order(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+              uint32_t *d_order, void *stream);
+
+/* Renumbering by position (Section 4.2, "How we use the vertex ordering"):
+ * d_rows_out[i] bit j = d_rows[d_order[i]] bit d_order[j], written with
+ * out_words_per_row words per row (extra words and bits zero).  The order's
+ * first vertex becomes bit 0, so "first in the order" is the lowest set bit
+ * (the paper stores the order reversed and scans from the top; Section 4.2). */
+int mce_renumber(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+                 const uint32_t *d_order, uint32_t out_words_per_row,
+                 uint32_t *d_rows_out, void *stream);
+
+/* Scratch bytes mce_search / mce_enumerate_device need for an n-vertex graph
+ * under the given options (NULL = defaults). */
+int mce_scratch_bytes(uint32_t n, const mce_options *opts, uint64_t *bytes);
+
+/* The search (Alg. 4) on an already renumbered graph: root P = V, X = {},
+ * pivot and branching by the chosen rule, per-warp explicit stacks,
+ * persistent work-stealing.  d_rows_renum has mce_search_words(n, opts)
+ * words per row; d_order maps position -> original label (for the hash).
+ * d_out receives MCE_OUT_WORDS(n) words. */
+int mce_search(uint32_t n, const uint32_t *d_rows_renum, const uint32_t *d_order,
+               const mce_options *opts, void *d_scratch, uint64_t scratch_bytes,
+               uint64_t *d_out, void *stream);
+
+/* Words per renumbered row that mce_search expects for these options. */
+uint32_t mce_search_words(uint32_t n, const mce_options *opts);
+
+/* The whole path on a device bitset: validate, order (unless
+ * MCE_ORDER_IDENTITY), renumber, search, reduce.  d_scratch must hold
+ * mce_scratch_bytes(n, opts) bytes. */
+int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+                         const mce_options *opts, void *d_scratch, uint64_t scratch_bytes,
+                         uint64_t *d_out, void *stream);
+
+/* ----------------------------------------------------------------------- */
+/* Host-level API: handles, host buffers, batching and serving.             */
+
+typedef struct mce_ctx mce_ctx;
+typedef struct mce_graph mce_graph;
+typedef uint64_t mce_ticket;
+
+typedef struct {
+    uint64_t count, nodes, internal_nodes, dead_ends, hash;
+    uint32_t max_size;
+    uint32_t status;              /* MCE_* code of this graph (batch/serve)  */
+    uint64_t *hist;               /* caller-owned, hist[k] for k < hist_cap  */
+    uint32_t hist_cap;
+    uint32_t _pad;
+    uint32_t *list_ids;           /* caller-owned, original labels           */
+    uint64_t list_cap;
+    uint64_t *list_off;           /* CSR offsets, count + 1 entries          */
+    uint64_t list_off_cap;
+    uint64_t list_ids_needed;
+    double kernel_ms, total_ms;
+} mce_result;
+
+/* Create a context on `device` with a device-memory budget (0 = 90% of
+ * free memory) and a stream (NULL = the library creates its own). */
+int mce_ctx_create(int device, uint64_t mem_budget_bytes, void *stream, mce_ctx **out);
+void mce_ctx_destroy(mce_ctx *ctx);
+
+/* Load a graph from m host edges (2*m uint32) or from a host bitset; both
+ * are copied to the device and canonicalised there (MCE_EINVAL on a
+ * self-loop, id >= n, asymmetry or set padding bits). */
+int mce_load_edges(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint64_t m, mce_graph **out);
+int mce_load_bitset(mce_ctx *ctx, uint32_t n, const uint32_t *rows, uint32_t words_per_row,
+                    mce_graph **out);
+void mce_graph_free(mce_graph *g);
+
+/* Enumerate one graph (plain form).  `res` is in/out: hist and list buffers
+ * are caller-owned; counters are filled.  MCE_ETRUNC if hist_cap <=
+ * max_size or the listing does not fit (counters still valid). */
+int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
+
+/* Enumerate `count` graphs in one persistent launch (batched form);
+ * res[i] belongs to graphs[i]. */
+int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
+                        const mce_options *opts, mce_result *res);
+
+/* Served form: requests are admitted by device memory and run with the
+ * others already on the GPU; mce_poll never blocks. */
+int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out);
+int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res);
+int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res);
+
+const char *mce_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCE_H */

@@ -1,0 +1,256 @@
+"""Python binding of libmce (include/mce.h).
+
+Argument marshalling only: every step of the search path runs in the CUDA
+kernels of ``libmce.so``.  There is no CPU fallback -- if the library is
+missing, ``lib()`` raises.  PyTorch is used by callers only for device memory
+and streams (tensors are passed by ``data_ptr()``).
+
+The functions keep the C names: ``mce_enumerate_device``, ``mce_search``,
+``mce_load_edges`` and so on.  ``Context`` / ``Graph`` wrap the handle API.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH, build  # noqa: F401
+
+MCE_OK, MCE_PENDING = 0, 1
+MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETRUNC = -1, -2, -3, -4
+MCE_ETIMEOUT, MCE_EOVERFLOW, MCE_ENOTIMPL = -5, -6, -7
+MCE_NMAX = 4096
+
+MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA = 0, 1, 2
+PIVOTS = {"greedy": 0, "tx": 1, "tomita": 2}
+MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED = 0x1, 0x2, 0x4
+
+MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
+MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
+MCE_OUT_HIST = 16
+
+
+def MCE_OUT_WORDS(n: int) -> int:
+    return MCE_OUT_HIST + n + 1
+
+
+class MceError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {mce_strerror(code)} ({code})" if what else f"{mce_strerror(code)} ({code})")
+
+
+class Options(C.Structure):
+    _fields_ = [("pivot_mode", C.c_uint32), ("flags", C.c_uint32), ("lanes_per_subtree", C.c_uint32),
+                ("words_per_lane", C.c_uint32), ("blocks", C.c_uint32), ("threads_per_block", C.c_uint32),
+                ("timeout_ns", C.c_uint64), ("stack_levels", C.c_uint32), ("_reserved", C.c_uint32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("count", C.c_uint64), ("nodes", C.c_uint64), ("internal_nodes", C.c_uint64),
+                ("dead_ends", C.c_uint64), ("hash", C.c_uint64), ("max_size", C.c_uint32),
+                ("status", C.c_uint32), ("hist", C.POINTER(C.c_uint64)), ("hist_cap", C.c_uint32),
+                ("_pad", C.c_uint32), ("list_ids", C.POINTER(C.c_uint32)), ("list_cap", C.c_uint64),
+                ("list_off", C.POINTER(C.c_uint64)), ("list_off_cap", C.c_uint64),
+                ("list_ids_needed", C.c_uint64), ("kernel_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+def options(pivot: str | int = "greedy", identity_order: bool = False, lanes: int = 0, words: int = 0,
+            blocks: int = 0, threads: int = 0, timeout_ns: int = 0, stack_levels: int = 0,
+            flags: int = 0) -> Options:
+    o = Options()
+    o.pivot_mode = PIVOTS[pivot] if isinstance(pivot, str) else int(pivot)
+    o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0)
+    o.lanes_per_subtree, o.words_per_lane = lanes, words
+    o.blocks, o.threads_per_block = blocks, threads
+    o.timeout_ns, o.stack_levels = timeout_ns, stack_levels
+    return o
+
+
+_lib = None
+_VP, _U32, _U64 = C.c_void_p, C.c_uint32, C.c_uint64
+
+_SIGS = {
+    "mce_edges_to_rows": (C.c_int, [_U32, _U64, _VP, _U32, _VP, _VP, _VP]),
+    "mce_validate_rows": (C.c_int, [_U32, _U32, _VP, _VP, _VP]),
+    "mce_order": (C.c_int, [_U32, _U32, _VP, _VP, _VP]),
+    "mce_renumber": (C.c_int, [_U32, _U32, _VP, _VP, _U32, _VP, _VP]),
+    "mce_scratch_bytes": (C.c_int, [_U32, C.POINTER(Options), C.POINTER(_U64)]),
+    "mce_search": (C.c_int, [_U32, _VP, _VP, C.POINTER(Options), _VP, _U64, _VP, _VP]),
+    "mce_search_words": (_U32, [_U32, C.POINTER(Options)]),
+    "mce_enumerate_device": (C.c_int, [_U32, _U32, _VP, C.POINTER(Options), _VP, _U64, _VP, _VP]),
+    "mce_ctx_create": (C.c_int, [C.c_int, _U64, _VP, C.POINTER(_VP)]),
+    "mce_ctx_destroy": (None, [_VP]),
+    "mce_load_edges": (C.c_int, [_VP, _U32, _VP, _U64, C.POINTER(_VP)]),
+    "mce_load_bitset": (C.c_int, [_VP, _U32, _VP, _U32, C.POINTER(_VP)]),
+    "mce_graph_free": (None, [_VP]),
+    "mce_enumerate": (C.c_int, [_VP, C.POINTER(Options), C.POINTER(Result)]),
+    "mce_enumerate_batch": (C.c_int, [_VP, C.POINTER(_VP), _U32, C.POINTER(Options), C.POINTER(Result)]),
+    "mce_submit": (C.c_int, [_VP, _VP, C.POINTER(Options), C.POINTER(_U64)]),
+    "mce_poll": (C.c_int, [_VP, _U64, C.POINTER(Result)]),
+    "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
+    "mce_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def lib():
+    """The loaded libmce.so; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libmce.so is not built ({_LIB_PATH}); run paper_1801_00202_gb300.build.build()")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _opt(o):
+    return C.byref(o if o is not None else Options())
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise MceError(rc, what)
+    return rc
+
+
+# --- C names, one to one ---------------------------------------------------
+
+def mce_strerror(code: int) -> str:
+    return lib().mce_strerror(code).decode()
+
+
+def mce_edges_to_rows(n, m, d_uv, words_per_row, d_rows, d_out, stream=None) -> int:
+    return lib().mce_edges_to_rows(n, m, _ptr(d_uv), words_per_row, _ptr(d_rows), _ptr(d_out), _stream(stream))
+
+
+def mce_validate_rows(n, words_per_row, d_rows, d_out, stream=None) -> int:
+    return lib().mce_validate_rows(n, words_per_row, _ptr(d_rows), _ptr(d_out), _stream(stream))
+
+
+def mce_order(n, words_per_row, d_rows, d_order, stream=None) -> int:
+    return lib().mce_order(n, words_per_row, _ptr(d_rows), _ptr(d_order), _stream(stream))
+
+
+def mce_renumber(n, words_per_row, d_rows, d_order, out_words_per_row, d_rows_out, stream=None) -> int:
+    return lib().mce_renumber(n, words_per_row, _ptr(d_rows), _ptr(d_order), out_words_per_row,
+                              _ptr(d_rows_out), _stream(stream))
+
+
+def mce_scratch_bytes(n, opts=None) -> int:
+    b = C.c_uint64(0)
+    _check(lib().mce_scratch_bytes(n, _opt(opts), C.byref(b)), "mce_scratch_bytes")
+    return int(b.value)
+
+
+def mce_search_words(n, opts=None) -> int:
+    return int(lib().mce_search_words(n, _opt(opts)))
+
+
+def mce_search(n, d_rows_renum, d_order, opts, d_scratch, scratch_bytes, d_out, stream=None) -> int:
+    return lib().mce_search(n, _ptr(d_rows_renum), _ptr(d_order), _opt(opts), _ptr(d_scratch), scratch_bytes,
+                            _ptr(d_out), _stream(stream))
+
+
+def mce_enumerate_device(n, words_per_row, d_rows, opts, d_scratch, scratch_bytes, d_out, stream=None) -> int:
+    return lib().mce_enumerate_device(n, words_per_row, _ptr(d_rows), _opt(opts), _ptr(d_scratch), scratch_bytes,
+                                      _ptr(d_out), _stream(stream))
+
+
+def decode_out(out, n: int) -> dict:
+    """Result dict from a device/host d_out array of MCE_OUT_WORDS(n) uint64."""
+    a = np.asarray(out.cpu().numpy() if hasattr(out, "cpu") else out).view(np.uint64)
+    return {"count": int(a[MCE_OUT_COUNT]), "nodes": int(a[MCE_OUT_NODES]),
+            "internal": int(a[MCE_OUT_INTERNAL]), "dead_ends": int(a[MCE_OUT_DEAD_ENDS]),
+            "hash": int(a[MCE_OUT_HASH]), "status": int(a[MCE_OUT_STATUS].astype(np.int64)),
+            "max_size": int(a[MCE_OUT_MAX_SIZE]), "donations": int(a[MCE_OUT_DONATIONS]),
+            "hist": a[MCE_OUT_HIST:MCE_OUT_HIST + n + 1].copy()}
+
+
+# --- handle API -------------------------------------------------------------
+
+class Context:
+    """mce_ctx: a device, a stream and a device-memory budget."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0, stream=None):
+        h = C.c_void_p()
+        _check(lib().mce_ctx_create(device, mem_budget, _stream(stream), C.byref(h)), "mce_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().mce_ctx_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_edges(self, n: int, uv) -> "Graph":
+        uv = np.ascontiguousarray(np.asarray(uv, dtype=np.uint32).reshape(-1, 2))
+        h = C.c_void_p()
+        _check(lib().mce_load_edges(self.handle, n, uv.ctypes.data if uv.size else None, uv.shape[0], C.byref(h)),
+               "mce_load_edges")
+        return Graph(self, h, n)
+
+    def load_bitset(self, n: int, rows) -> "Graph":
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32))
+        w = rows.shape[1] if rows.ndim == 2 else max(1, (n + 31) // 32)
+        h = C.c_void_p()
+        _check(lib().mce_load_bitset(self.handle, n, rows.ctypes.data if rows.size else None, w, C.byref(h)),
+               "mce_load_bitset")
+        return Graph(self, h, n)
+
+
+class Graph:
+    """mce_graph: a validated graph resident on the device."""
+
+    def __init__(self, ctx: Context, handle, n: int):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def free(self):
+        if self.handle:
+            lib().mce_graph_free(self.handle)
+            self.handle = None
+
+    __del__ = free
+
+    def enumerate(self, opts: Options | None = None, raise_on_error: bool = True) -> dict:
+        hist = np.zeros(self.n + 1, dtype=np.uint64)
+        r = Result()
+        r.hist = hist.ctypes.data_as(C.POINTER(C.c_uint64))
+        r.hist_cap = hist.size
+        rc = lib().mce_enumerate(self.handle, _opt(opts), C.byref(r))
+        if raise_on_error:
+            _check(rc, "mce_enumerate")
+        return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
+                "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
+                "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}

@@ -1,0 +1,216 @@
+// Preprocessing steps of the search path on the device:
+//  * input canonicalisation (Section 2: simple undirected graph) from an edge
+//    list or a bitset,
+//  * the maximum-degree-first ordering (Section 4.2),
+//  * renumbering by position (Section 4.2, "How we use the vertex ordering").
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mce_internal.h"
+
+namespace mce {
+namespace {
+
+constexpr unsigned FULLM = 0xffffffffu;
+
+__device__ __forceinline__ void flag_invalid(uint64_t *out)
+{
+    atomicCAS(reinterpret_cast<unsigned long long *>(out + MCE_OUT_STATUS), 0ull,
+              static_cast<unsigned long long>(static_cast<long long>(MCE_EINVAL)));
+}
+
+// Edge list -> symmetric bitset (rows cleared beforehand).
+__global__ void edges_kernel(uint32_t n, uint64_t m, const uint32_t *__restrict__ uv, uint32_t w,
+                             uint32_t *__restrict__ rows, uint64_t *out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t a = uv[2 * e], b = uv[2 * e + 1];
+        if (a >= n || b >= n || a == b) {
+            flag_invalid(out);
+            continue;
+        }
+        atomicOr(rows + (size_t)a * w + (b >> 5), 1u << (b & 31));
+        atomicOr(rows + (size_t)b * w + (a >> 5), 1u << (a & 31));
+    }
+}
+
+// Bitset checks: zero diagonal, zero bits at positions >= n, symmetry.
+__global__ void validate_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows, uint64_t *out)
+{
+    const uint64_t total = (uint64_t)n * w;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const uint32_t i = (uint32_t)(idx / w), j = (uint32_t)(idx % w);
+        uint32_t word = rows[idx];
+        if (word == 0u) continue;
+        const uint32_t base = j * 32u;
+        uint32_t valid = FULLM;
+        if (base >= n) valid = 0u;
+        else if (n - base < 32u) valid = (1u << (n - base)) - 1u;
+        if (word & ~valid) { flag_invalid(out); continue; }
+        if (i >= base && i < base + 32u && ((word >> (i - base)) & 1u)) { flag_invalid(out); continue; }
+        while (word) {
+            const uint32_t b = (uint32_t)__ffs(word) - 1u;
+            word &= word - 1u;
+            const uint32_t u = base + b;
+            if (!((rows[(size_t)u * w + (i >> 5)] >> (i & 31)) & 1u)) { flag_invalid(out); break; }
+        }
+    }
+}
+
+// Maximum-degree-first order.  The block stages the rows in shared memory
+// (when they fit) and computes all degrees; then warp 0 runs the n rounds
+// with the keys in registers: lane l owns the vertices of words
+// [l*JW, l*JW + JW), key = (degree + 1) << 12 | (4095 - u) while u is not
+// placed (0 once placed), so the maximum key is the highest remaining degree
+// with the smallest label.  A round takes the warp maximum, places that
+// vertex and decrements the keys of its remaining neighbours.
+template <int JW>
+__global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
+                                                   uint32_t *__restrict__ order, int rows_in_smem)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *sdeg = sm;                                  // n keys
+    uint32_t *srows = sm + ((n + 3u) & ~3u);              // n * w words (optional)
+    const uint32_t *R = rows;
+    if (rows_in_smem) {
+        for (uint32_t i = threadIdx.x; i < n * w; i += blockDim.x) srows[i] = rows[i];
+        R = srows;
+    }
+    __syncthreads();
+    for (uint32_t u = threadIdx.x; u < n; u += blockDim.x) {
+        uint32_t deg = 0;
+        for (uint32_t j = 0; j < w; ++j) deg += __popc(R[(size_t)u * w + j]);
+        sdeg[u] = ((deg + 1u) << 12) | (4095u - u);
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+
+    const uint32_t lane = threadIdx.x;
+    uint32_t key[32 * JW];
+#pragma unroll
+    for (int q = 0; q < JW; ++q)
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t u = (lane * JW + q) * 32u + b;
+            key[q * 32 + b] = u < n ? sdeg[u] : 0u;
+        }
+
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t best = 0;
+#pragma unroll
+        for (int t = 0; t < 32 * JW; ++t) best = key[t] > best ? key[t] : best;
+        best = __reduce_max_sync(FULLM, best);
+        const uint32_t v = 4095u - (best & 4095u);
+        if (lane == 0) order[i] = v;
+        const uint32_t *rv = R + (size_t)v * w;
+#pragma unroll
+        for (int q = 0; q < JW; ++q) {
+            const uint32_t wi = lane * JW + q;
+            const uint32_t word = wi < w ? rv[wi] : 0u;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                uint32_t k = key[q * 32 + b];
+                if (wi * 32u + b == v) k = 0u;
+                else if (((word >> b) & 1u) && k) k -= 1u << 12;
+                key[q * 32 + b] = k;
+            }
+        }
+    }
+}
+
+__global__ void identity_kernel(uint32_t n, uint32_t *order)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) order[i] = i;
+}
+
+// A'[i][j] = A[order[i]][order[j]]: one warp per output word, each lane
+// fetching one bit and a ballot assembling the word.
+__global__ void renumber_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
+                                const uint32_t *__restrict__ order, uint32_t wout, uint32_t *__restrict__ out)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t total = (uint64_t)n * wout;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += nwarps) {
+        const uint32_t i = (uint32_t)(t / wout), jw = (uint32_t)(t % wout);
+        const uint32_t j = jw * 32u + lane;
+        bool bit = false;
+        if (j < n) {
+            const uint32_t src = __ldg(order + i), col = __ldg(order + j);
+            bit = (__ldg(rows + (size_t)src * w + (col >> 5)) >> (col & 31)) & 1u;
+        }
+        const uint32_t word = __ballot_sync(FULLM, bit);
+        if (lane == 0) out[t] = word;
+    }
+}
+
+unsigned grid_for(uint64_t work, unsigned threads)
+{
+    uint64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 65535u) g = 65535u;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t launch_edges_to_rows(uint32_t n, uint64_t m, const uint32_t *uv, uint32_t w, uint32_t *rows,
+                                 uint64_t *out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(rows, 0, (size_t)n * w * 4, s);
+    if (e != cudaSuccess || m == 0) return e;
+    edges_kernel<<<grid_for(m, 256), 256, 0, s>>>(n, m, uv, w, rows, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_rows(uint32_t n, uint32_t w, const uint32_t *rows, uint64_t *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    validate_kernel<<<grid_for((uint64_t)n * w, 256), 256, 0, s>>>(n, w, rows, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t *order, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t keys = ((n + 3u) & ~3u) * sizeof(uint32_t);
+    const size_t rbytes = (size_t)n * w * 4;
+    const int in_smem = (keys + rbytes) <= 200u * 1024u;
+    const size_t smem = keys + (in_smem ? rbytes : 0);
+    const uint32_t words = (n + 31) / 32;  // words that can hold set bits
+    cudaError_t e;
+    if (words <= 32) {
+        e = cudaFuncSetAttribute(order_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        order_kernel<1><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
+    } else if (words <= 64) {
+        e = cudaFuncSetAttribute(order_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        order_kernel<2><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
+    } else {
+        e = cudaFuncSetAttribute(order_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        order_kernel<4><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity(uint32_t n, uint32_t *order, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    identity_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_renumber(uint32_t n, uint32_t w, const uint32_t *rows, const uint32_t *order, uint32_t wout,
+                            uint32_t *rows_out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t warps = (uint64_t)n * wout;
+    renumber_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(n, w, rows, order, wout, rows_out);
+    return cudaGetLastError();
+}
+
+}  // namespace mce

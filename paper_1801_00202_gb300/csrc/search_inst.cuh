@@ -1,0 +1,65 @@
+// Launch wrappers for one (lanes per group, words per lane) instantiation of
+// the search kernel; each search_gN.cu instantiates a few of them so the
+// library compiles in parallel.
+#pragma once
+
+#include "search_impl.cuh"
+
+namespace mce {
+
+template <int G, int K, bool SMEM, int PIVOT>
+cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStream_t s)
+{
+    const unsigned *rp = nullptr;
+    if (PIVOT == MCE_PIVOT_TOMITA && prm.n > 0) {
+        unsigned *dst = &prm.ctl->pad4[0];
+        root_tomita_pivot_kernel<0><<<1, 1024, 0, s>>>(prm.rows, prm.n, prm.wp, dst);
+        rp = dst;
+    }
+    search_init_kernel<G, K><<<64, 256, 0, s>>>(prm, rp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    search_kernel<G, K, SMEM, PIVOT><<<sh.blocks, sh.threads, sh.smem, s>>>(prm);
+    return cudaGetLastError();
+}
+
+template <int G, int K, bool SMEM, int PIVOT>
+cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<G, K, SMEM, PIVOT>, threads,
+                                                         smem);
+}
+
+template <int G, int K, bool SMEM>
+SearchImpl pick_pivot(int pivot)
+{
+    switch (pivot) {
+    case MCE_PIVOT_GREEDY: return {run_search_t<G, K, SMEM, MCE_PIVOT_GREEDY>, occupancy_t<G, K, SMEM, MCE_PIVOT_GREEDY>};
+    case MCE_PIVOT_GREEDY_TX:
+        return {run_search_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>, occupancy_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>};
+    case MCE_PIVOT_TOMITA: return {run_search_t<G, K, SMEM, MCE_PIVOT_TOMITA>, occupancy_t<G, K, SMEM, MCE_PIVOT_TOMITA>};
+    default: return {nullptr, nullptr};
+    }
+}
+
+// Rows live in shared memory only for sets of at most 32 words.
+template <int G, int K>
+SearchImpl pick(bool smem, int pivot)
+{
+    if constexpr (G * K <= 32) {
+        if (smem) return pick_pivot<G, K, true>(pivot);
+    }
+    if (smem) return {nullptr, nullptr};
+    return pick_pivot<G, K, false>(pivot);
+}
+
+}  // namespace mce
+
+#define MCE_DEFINE_SEARCH(G, K) \
+    namespace mce { SearchImpl search_impl_##G##_##K(bool smem, int pivot) { return pick<G, K>(smem, pivot); } }

@@ -1,0 +1,48 @@
+"""The C-ABI library loads and exports every function include/mce.h
+declares (no GPU needed: nothing here launches a kernel)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mce.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mce_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1801_00202_gb300 as m
+    m.build()
+    return m.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("mce_load_edges", "mce_load_bitset", "mce_enumerate", "mce_submit", "mce_poll",
+                 "mce_enumerate_device", "mce_search", "mce_order", "mce_renumber"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    import paper_1801_00202_gb300 as m
+    assert set(declared_functions()) <= set(m._SIGS)
+
+
+def test_host_only_calls(lib):
+    import paper_1801_00202_gb300 as m
+    assert m.mce_strerror(m.MCE_EINVAL) == "invalid argument or graph"
+    assert m.mce_strerror(m.MCE_OK) == "ok"
+    # argument checks happen before any CUDA call
+    assert m.mce_order(m.MCE_NMAX + 1, 200, 0, 0) == m.MCE_EINVAL
+    assert m.mce_renumber(10, 0, 0, 0, 1, 0) == m.MCE_EINVAL
+    assert m.mce_enumerate_device(10, 1, None, None, None, 0, None) == m.MCE_EINVAL

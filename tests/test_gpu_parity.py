@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Everything the search computes is integer/bitwise, so every comparison is
+exact: count, histogram, hash (against Alg. 2 with the Tomita pivot), and the
+search-tree counters nodes / internal / dead ends (against the oracle's
+Alg. 4 tree for the same pivot rule and order).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def mce():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_00202_gb300 as m
+    m.build()
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mce):
+    c = mce.Context(0)
+    yield c
+    c.close()
+
+
+def run_host(ctx, mce, n, uv, **kw):
+    g = ctx.load_edges(n, uv)
+    try:
+        return g.enumerate(mce.options(**kw))
+    finally:
+        g.free()
+
+
+def expect_equal(got, n, uv, mode="greedy", order=None, what=""):
+    ref = oracle.tomita(n, uv)
+    tree = oracle.ordered(n, uv, mode, order=order)
+    assert got["count"] == ref["count"], what
+    assert np.array_equal(np.asarray(got["hist"], dtype=np.uint64), ref["hist"]), what
+    assert got["hash"] == ref["hash"], what
+    assert (got["nodes"], got["internal"], got["dead_ends"]) == \
+        (tree["nodes"], tree["internal"], tree["dead_ends"]), what
+
+
+# --- random graphs across word and group boundaries -------------------------
+
+CASES = [(1, 0.5, 1), (2, 1.0, 2), (5, 0.5, 3), (31, 0.5, 4), (32, 0.5, 5), (33, 0.6, 6), (63, 0.5, 7),
+         (64, 0.7, 8), (65, 0.5, 9), (100, 0.5, 0), (127, 0.4, 10), (128, 0.5, 11), (129, 0.3, 12),
+         (200, 0.4, 13), (257, 0.3, 14), (300, 0.3, 15), (513, 0.15, 16), (700, 0.1, 17),
+         (1025, 0.05, 18), (1500, 0.03, 19), (2049, 0.01, 20), (4096, 0.004, 21)]
+
+
+@pytest.mark.parametrize("n,p,seed", CASES)
+def test_random_graph(ctx, mce, n, p, seed):
+    uv = synth.gnp(n, p, seed)
+    expect_equal(run_host(ctx, mce, n, uv), n, uv, what=f"G({n},{p}) seed {seed}")
+
+
+@pytest.mark.parametrize("mode", ["tx", "tomita"])
+@pytest.mark.parametrize("n,p,seed", [(50, 0.5, 30), (100, 0.5, 0), (200, 0.3, 31), (700, 0.1, 32)])
+def test_pivot_rules(ctx, mce, mode, n, p, seed):
+    uv = synth.gnp(n, p, seed)
+    expect_equal(run_host(ctx, mce, n, uv, pivot=mode), n, uv, mode=mode, what=f"{mode} G({n},{p})")
+
+
+SHAPES = [(1, 1), (1, 2), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (16, 2), (32, 1), (32, 2),
+          (32, 4)]
+
+
+@pytest.mark.parametrize("n,p,seed", [(30, 0.6, 40), (60, 0.5, 41), (120, 0.5, 42)])
+def test_every_lane_shape_gives_the_same_tree(ctx, mce, n, p, seed):
+    uv = synth.gnp(n, p, seed)
+    ref = oracle.tomita(n, uv)
+    tree = oracle.ordered(n, uv)
+    W = (n + 31) // 32
+    for lanes, words in SHAPES:
+        if lanes * words < W:
+            continue
+        got = run_host(ctx, mce, n, uv, lanes=lanes, words=words)
+        assert (got["count"], got["hash"]) == (ref["count"], ref["hash"]), (lanes, words)
+        assert np.array_equal(got["hist"], ref["hist"]), (lanes, words)
+        assert (got["nodes"], got["internal"], got["dead_ends"]) == \
+            (tree["nodes"], tree["internal"], tree["dead_ends"]), (lanes, words)
+
+
+@pytest.mark.parametrize("kw", [dict(blocks=1, threads=32), dict(blocks=3, threads=64), dict(stack_levels=1),
+                                dict(stack_levels=2, blocks=1, threads=32), dict(stack_levels=3, lanes=4, words=1)])
+def test_work_splitting_does_not_change_results(ctx, mce, kw):
+    n, uv = 90, synth.gnp(90, 0.5, 50)
+    expect_equal(run_host(ctx, mce, n, uv, **kw), n, uv, what=str(kw))
+
+
+# --- closed forms and degenerate graphs -------------------------------------
+
+def test_zero_and_one_vertex(ctx, mce):
+    r0 = run_host(ctx, mce, 0, synth.empty(0))
+    assert (r0["count"], r0["nodes"], int(r0["hist"][0])) == (1, 1, 1)
+    assert r0["hash"] == oracle.clique_hash([])
+    r1 = run_host(ctx, mce, 1, synth.empty(1))
+    assert (r1["count"], r1["nodes"], r1["internal"]) == (1, 2, 1)
+    assert r1["hash"] == oracle.clique_hash([0])
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9, 12])
+def test_moon_moser(ctx, mce, k):
+    r = run_host(ctx, mce, 3 * k, synth.moon_moser(k))
+    assert r["count"] == 3 ** k and int(r["hist"][k]) == 3 ** k
+    assert r["nodes"] == (3 ** (k + 1) - 1) // 2 and r["dead_ends"] == 0
+
+
+@pytest.mark.parametrize("n", [2, 33, 500, 1000, 4096])
+def test_complete_graph_chain(ctx, mce, n):
+    r = run_host(ctx, mce, n, synth.complete(n))
+    assert r["count"] == 1 and int(r["hist"][n]) == 1
+    assert r["hash"] == oracle.clique_hash(np.arange(n))
+    assert (r["nodes"], r["internal"], r["dead_ends"]) == (n + 1, n, 0)
+
+
+@pytest.mark.parametrize("n", [3, 64, 1000, 4096])
+def test_empty_graph(ctx, mce, n):
+    r = run_host(ctx, mce, n, synth.empty(n))
+    assert r["count"] == n and int(r["hist"][1]) == n
+    assert (r["nodes"], r["internal"]) == (n + 1, 1)
+
+
+@pytest.mark.parametrize("sizes", [(2, 3, 4), (5, 5, 5, 5), (1, 7, 2, 3, 9)])
+def test_complete_multipartite(ctx, mce, sizes):
+    n = sum(sizes)
+    r = run_host(ctx, mce, n, synth.complete_multipartite(sizes))
+    assert r["count"] == int(np.prod(sizes)) and int(r["hist"][len(sizes)]) == int(np.prod(sizes))
+
+
+def test_section5_example_identity_order(ctx, mce):
+    labels = [2, 4, 5, 6, 7, 8, 9]
+    idx = {v: i for i, v in enumerate(labels)}
+    edges = [(9, 8), (9, 7), (9, 6), (9, 5), (9, 4), (9, 2), (8, 7), (8, 2), (7, 2), (6, 2), (6, 5), (6, 4)]
+    order = [9, 8, 7, 6, 5, 4, 2]
+    # relabel so that the given order is the identity
+    pos = {v: i for i, v in enumerate(order)}
+    uv = np.array([[pos[a], pos[b]] for a, b in edges], dtype=np.uint32)
+    for mode in ("greedy", "tomita"):
+        got = run_host(ctx, mce, 7, uv, pivot=mode, identity_order=True)
+        expect_equal(got, 7, uv, mode=mode, order=np.arange(7, dtype=np.uint32))
+        assert got["count"] == 4
+    assert idx  # labels documented above
+
+
+# --- invalid input and bounded waits ----------------------------------------
+
+def test_invalid_inputs(ctx, mce):
+    with pytest.raises(mce.MceError) as e:
+        ctx.load_edges(4, np.array([[0, 1], [2, 2]], dtype=np.uint32))
+    assert e.value.code == mce.MCE_EINVAL
+    with pytest.raises(mce.MceError) as e:
+        ctx.load_edges(4, np.array([[0, 4]], dtype=np.uint32))
+    assert e.value.code == mce.MCE_EINVAL
+    rows = synth.to_bitset(40, synth.gnp(40, 0.5, 60))
+    bad = rows.copy()
+    bad[3, 0] ^= np.uint32(1 << 7)          # asymmetric (or breaks the diagonal)
+    with pytest.raises(mce.MceError):
+        ctx.load_bitset(40, bad)
+    pad = rows.copy()
+    pad[5, 1] |= np.uint32(1 << 20)         # bit 52 >= n
+    with pytest.raises(mce.MceError):
+        ctx.load_bitset(40, pad)
+    g = ctx.load_bitset(40, rows)           # the valid one still loads
+    assert g.enumerate()["count"] == oracle.tomita(40, synth.gnp(40, 0.5, 60))["count"]
+    g.free()
+
+
+def test_timeout_is_reported_and_context_survives(ctx, mce):
+    n, uv = 36, synth.moon_moser(12)
+    g = ctx.load_edges(n, uv)
+    r = g.enumerate(mce.options(timeout_ns=1), raise_on_error=False)
+    assert r["rc"] in (mce.MCE_ETIMEOUT, mce.MCE_OK)
+    ok = g.enumerate()
+    assert ok["count"] == 3 ** 12
+    g.free()
+
+
+# --- device-level calls with torch-owned memory -----------------------------
+
+def test_device_steps_match_oracle(mce):
+    import torch
+    n, uv = 300, synth.gnp(300, 0.3, 70)
+    W = (n + 31) // 32
+    dev = torch.device("cuda:0")
+    s = torch.cuda.current_stream()
+    d_uv = torch.from_numpy(uv.astype(np.int32).reshape(-1)).to(dev)
+    rows = torch.zeros(n * W, dtype=torch.int32, device=dev)
+    out = torch.zeros(mce.MCE_OUT_WORDS(n), dtype=torch.int64, device=dev)
+    assert mce.mce_edges_to_rows(n, uv.shape[0], d_uv, W, rows, out, s) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(rows.cpu().numpy().view(np.uint32).reshape(n, W), synth.to_bitset(n, uv))
+    order = torch.zeros(n, dtype=torch.int32, device=dev)
+    assert mce.mce_order(n, W, rows, order, s) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(order.cpu().numpy().view(np.uint32), oracle.mdf_order(n, uv))
+    o = mce.options()
+    wp = mce.mce_search_words(n, o)
+    ren = torch.zeros(n * wp + 4, dtype=torch.int32, device=dev)
+    assert mce.mce_renumber(n, W, rows, order, wp, ren, s) == 0
+    torch.cuda.synchronize()
+    A = synth.to_bitset(n, uv)
+    dense = np.unpackbits(A.view(np.uint8), bitorder="little").reshape(n, -1)[:, :n]
+    perm = oracle.mdf_order(n, uv)
+    want = np.packbits(dense[np.ix_(perm, perm)], axis=1, bitorder="little")
+    want = np.pad(want, ((0, 0), (0, wp * 4 - want.shape[1]))).view(np.uint32)
+    assert np.array_equal(ren.cpu().numpy().view(np.uint32)[:n * wp].reshape(n, wp), want)
+    nbytes = mce.mce_scratch_bytes(n, o)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    assert mce.mce_search(n, ren, order, o, scratch, nbytes, out, s) == 0
+    torch.cuda.synchronize()
+    expect_equal(mce.decode_out(out, n), n, uv)
+    # the whole path in one call, twice on the same scratch
+    for _ in range(2):
+        out.zero_()
+        assert mce.mce_enumerate_device(n, W, rows, o, scratch, nbytes, out, s) == 0
+        torch.cuda.synchronize()
+        got = mce.decode_out(out, n)
+        assert got["status"] == 0
+        expect_equal(got, n, uv)
+
+
+# --- full-size workloads (expected values from the oracle, stored) ----------
+
+def _golden():
+    p = os.path.join(GOLDEN, "config_results.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+WORKLOADS = {
+    "gnp_100_0.5_s0": lambda: (100, synth.gnp(100, 0.5, 0)),
+    "gnp_1000_0.3_s1": lambda: (1000, synth.gnp(1000, 0.3, 1)),
+    "moon_moser_45": lambda: (45, synth.moon_moser(15)),
+    "moon_moser_45_del5": lambda: (45, synth.moon_moser_deleted(15, 0.05, 3)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_full_size_workload(ctx, mce, name):
+    gold = _golden().get(name)
+    if gold is None:
+        pytest.skip("expected values not generated")
+    n, uv = WORKLOADS[name]()
+    got = run_host(ctx, mce, n, uv)
+    assert got["count"] == gold["count"]
+    assert got["hash"] == gold["hash"]
+    hist = {str(k): int(v) for k, v in enumerate(got["hist"]) if v}
+    assert hist == gold["hist"]
+    t = gold["greedy"]
+    assert (got["nodes"], got["internal"], got["dead_ends"]) == (t["nodes"], t["internal"], t["dead_ends"])
