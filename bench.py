@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the maximal clique enumeration path on GB300.
+
+One *step* is one pass of the whole search path over one synthetic graph
+already resident in HBM: input validation, maximum-degree-first ordering,
+renumbering, the search itself and the reduction (every kernel of
+mce_enumerate_device, called step by step so the search launch can be timed
+on its own).  The workload is G(n = 1000, p = 0.3) with seed 1, the shape of
+the paper's Table 1 row n = 1000, p = 0.3.
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  ``value`` is maximal cliques per second over
+all ranks (each rank runs its own replica: the plain form does not shard).
+``e2e`` is the same metric through the handle API from pinned host memory
+(mce_load_edges + mce_enumerate + mce_graph_free).  ``--impl reference``
+times the CPU oracle (Bron-Kerbosch with the Tomita pivot) on bounded samples
+of the same graph on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "maximal cliques/s & BK nodes/s, plain vs batched/served; p50/p99 latency"
+UNIT = "maximal cliques/s"
+# name -> (n, p, seed); the default is the measured workload, the others are
+# smaller cases of the same kernels for profiling.
+WORKLOADS = {
+    "gnp_1000_0.3_s1": (1000, 0.3, 1),
+    "gnp_700_0.3_s2": (700, 0.3, 2),
+    "gnp_100_0.5_s0": (100, 0.5, 0),
+}
+DEFAULT_WORKLOAD = "gnp_1000_0.3_s1"
+N, P, SEED = WORKLOADS[DEFAULT_WORKLOAD]
+WORKLOAD = ""
+GOLDEN_KEY = DEFAULT_WORKLOAD
+
+
+def select_workload(name: str):
+    global N, P, SEED, WORKLOAD, GOLDEN_KEY
+    N, P, SEED = WORKLOADS[name]
+    GOLDEN_KEY = name
+    WORKLOAD = (f"G(n={N}, p={P}) seed {SEED}, one graph, plain form "
+                f"(whole path: validate, order, renumber, search, reduce)")
+# Table 1, n = 1000, p = 0.3: GreedyBB found 15.487755M cliques in 4.964 s on one
+# Xeon E5-2690 v2 core (10-graph mean; other instances of the same shape).
+PAPER_CLIQUES_PER_S = 15487755 / 4.964
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+# Roofline denominators derived from the GB300 unit counts and maximum clock:
+# 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz lane-operations per second (one
+# warp instruction per scheduler per clock), and 152 SMs x 128 B/clk x 2.07 GHz
+# of shared-memory bandwidth.
+SMS, SM_MHZ = 152, 2070.0
+ALU_PEAK_OPS = SMS * 4 * 32 * SM_MHZ * 1e6
+SMEM_PEAK_BPS = SMS * 128 * SM_MHZ * 1e6
+ORACLE_SAMPLE_NODES = 1_500_000     # per reference step
+BASELINE_SAMPLE_NODES = 5_000_000   # cpu_baseline leg (about 10-30 s)
+
+
+def words(n: int) -> int:
+    return max(1, (n + 31) // 32)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            t = [x.strip() for x in line.split(",")]
+            if len(t) >= 7:
+                rows.append(t)
+        os.unlink(self.path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def golden():
+    p = os.path.join(ROOT, "tests", "golden", "config_results.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get(GOLDEN_KEY)
+    return None
+
+
+def base_line(args, world):
+    return {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "p": P, "seed": SEED, "words_per_row": words(N),
+                       "l2": "flushed between timed steps (256 MiB write)", "replicas": world}}
+
+
+def cpu_baseline(uv, max_nodes: int) -> dict:
+    import oracle
+    t = time.perf_counter()
+    r = oracle.tomita(N, uv, max_nodes=max_nodes)
+    dt = time.perf_counter() - t
+    return {"value": r["count"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"Bron-Kerbosch with the Tomita pivot on the same graph, first {r['nodes']} search nodes "
+                      f"({r['count']} maximal cliques, {dt:.1f} s on one host core)",
+            "nodes_per_s": r["nodes"] / dt}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    uv = synth.gnp(N, P, SEED)
+    rates, times = [], []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        r = oracle.tomita(N, uv, max_nodes=ORACLE_SAMPLE_NODES)
+        dt = time.perf_counter() - t
+        if i >= args.warmup:
+            rates.append(r["count"] / dt)
+            times.append(dt)
+    value = statistics.mean(rates)
+    line = base_line(args, world)
+    line.update({"impl": "reference", "value": value, "ms_per_step": 1e3 * statistics.mean(times),
+                 "vs_baseline": value / PAPER_CLIQUES_PER_S,
+                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"each step: Bron-Kerbosch with the Tomita pivot on the same graph, "
+                                            f"first {ORACLE_SAMPLE_NODES} search nodes, one host core"},
+                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1801_00202_gb300 as mce
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mce.build()
+    mce.lib()
+
+    uv = synth.gnp(N, P, SEED)
+    W = words(N)
+    opts = mce.options()
+    wp = mce.mce_search_words(N, opts)
+    s = torch.cuda.Stream(device=dev)
+    rows = torch.from_numpy(synth.to_bitset(N, uv).view(np.int32).reshape(-1)).to(dev)
+    order = torch.zeros(N, dtype=torch.int32, device=dev)
+    ren = torch.zeros(N * wp + 4, dtype=torch.int32, device=dev)
+    nbytes = mce.mce_scratch_bytes(N, opts)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = torch.zeros(mce.MCE_OUT_WORDS(N), dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(ev0, ev1, ev2):
+        with torch.cuda.stream(s):
+            ev0.record(s)
+            out.zero_()
+            rc = mce.mce_validate_rows(N, W, rows, out, s)
+            rc = rc or mce.mce_order(N, W, rows, order, s)
+            rc = rc or mce.mce_renumber(N, W, rows, order, wp, ren, s)
+            ev1.record(s)
+            rc = rc or mce.mce_search(N, ren, order, opts, scratch, nbytes, out, s)
+            ev2.record(s)
+        if rc:
+            raise mce.MceError(rc, "step")
+
+    def flush_l2():
+        with torch.cuda.stream(s):
+            flush.zero_()
+
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(args.warmup):
+        flush_l2()
+        step(mk(), mk(), mk())
+    torch.cuda.synchronize()
+    res = mce.decode_out(out, N)
+    if res["status"] != 0:
+        raise mce.MceError(res["status"], "warm-up")
+
+    clocks = ClockSampler(local)
+    evs = [(mk(), mk(), mk()) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for e in evs:
+        flush_l2()
+        step(*e)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(c) for a, b, c in evs]
+    search_ms = [b.elapsed_time(c) for a, b, c in evs]
+    prep_ms = [a.elapsed_time(b) for a, b, c in evs]
+    res = mce.decode_out(out, N)
+    if res["status"] != 0:
+        raise mce.MceError(res["status"], "timed steps")
+
+    # --- end to end through the handle API, host buffers in pinned memory
+    e2e_s, r2 = [], {"count": res["count"]}
+    if not args.no_e2e:
+        ctx = mce.Context(local, stream=s)
+        pinned = torch.from_numpy(uv.astype(np.int32)).pin_memory()
+        host_uv = pinned.numpy().view(np.uint32)
+        for _ in range(args.warmup):
+            g = ctx.load_edges(N, host_uv)
+            g.enumerate(opts)
+            g.free()
+        for _ in range(args.steps):
+            flush_l2()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            g = ctx.load_edges(N, host_uv)
+            r2 = g.enumerate(opts)
+            g.free()
+            e2e_s.append(time.perf_counter() - t)
+        ctx.close()
+    clk = clocks.stop()
+
+    total_ms = float(sum(step_ms))
+    e2e_total = float(sum(e2e_s)) if e2e_s else 0.0
+    if dist:
+        t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_total = float(t[0]), float(t[1])
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    count, nodes = res["count"], res["nodes"]
+    value = world * args.steps * count / (total_ms / 1e3)
+    gold = golden()
+    check = {"status": res["status"], "count": count, "nodes": nodes, "hash": res["hash"]}
+    if gold:
+        check["matches_oracle"] = (count == gold["count"] and res["hash"] == gold["hash"]
+                                   and nodes == gold["greedy"]["nodes"] and r2["count"] == gold["count"])
+    search_avg = statistics.mean(search_ms)
+    ops = 6 * W * nodes                 # algorithmic 32-bit lane-ops per search launch
+    smem_bytes = 8 * W * nodes          # two adjacency rows per node
+    line = base_line(args, world)
+    line.update({
+        "impl": "ours",
+        "value": value,
+        "ms_per_step": total_ms / args.steps,
+        "vs_baseline": value / PAPER_CLIQUES_PER_S,
+        "vs_baseline_note": "paper's GreedyBB, Table 1 n=1000 p=0.3 (10-graph mean, one Xeon E5-2690 v2 core)",
+        "nodes_per_s": world * args.steps * nodes / (total_ms / 1e3),
+        "breakdown_ms": {"prep (validate+order+renumber)": statistics.mean(prep_ms),
+                         "search (init+persistent kernel)": search_avg,
+                         "wall_per_step_incl_l2_flush": 1e3 * t_wall / args.steps},
+        "check": check,
+        "roofline": {"bound": "alu", "kernel": "search_kernel",
+                     "achieved": ops / (search_avg / 1e3) / 1e12, "peak": ALU_PEAK_OPS / 1e12,
+                     "unit": "Tops/s (32-bit lane ops)", "frac": ops / (search_avg / 1e3) / ALU_PEAK_OPS,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz",
+                     "ops_per_node": 6 * W, "nodes_per_launch": nodes},
+        "roofline_smem": {"achieved": smem_bytes / (search_avg / 1e3) / 1e9, "peak": SMEM_PEAK_BPS / 1e9,
+                          "unit": "GB/s", "frac": smem_bytes / (search_avg / 1e3) / SMEM_PEAK_BPS,
+                          "bytes_per_node": 8 * W,
+                          "peak_source": "derived: 152 SMs x 128 B/clk x 2.07 GHz"},
+        "e2e": None if args.no_e2e else {
+            "value": world * args.steps * r2["count"] / e2e_total, "unit": UNIT,
+            "h2d_bytes_per_step": int(uv.shape[0]) * 8,
+            "d2h_bytes_per_step": mce.MCE_OUT_WORDS(N) * 8 + 8,
+            "ms_per_step": 1e3 * e2e_total / args.steps,
+            "api": "mce_load_edges (pinned host edge list) + mce_enumerate + mce_graph_free"},
+        "gpu_launches": 5 * args.steps + (0 if args.no_e2e else 6 * args.steps),
+        "clocks": clk,
+    })
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(uv, BASELINE_SAMPLE_NODES)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    args = ap.parse_args()
+    select_workload(args.workload)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -102,7 +102,10 @@ typedef struct {
     uint32_t stack_levels;      /* explicit-stack levels per subtree before
                                    frames spill to the device work queue,
                                    1..64; 0 = 64                              */
-    uint32_t _reserved;
+    uint32_t queue_log2;        /* log2 of the device work-queue slots, <= 24;
+                                   0 = auto (at least twice the subtree
+                                   groups).  mce_enumerate retries a search
+                                   that overflowed with a 16x larger queue.   */
 } mce_options;
 
 /* Layout of the device result array d_out (uint64 words, zeroed and filled

@@ -58,7 +58,7 @@ def _load():
         lib.oracle_mdf_order.restype = None
         lib.oracle_mdf_order.argtypes = [C.c_uint32, u32p, u32p, u32p]
         lib.oracle_tomita.restype = C.c_int
-        lib.oracle_tomita.argtypes = [C.c_uint32, u32p, u32p, u64p, u64p, u32p, C.c_uint64, u64p]
+        lib.oracle_tomita.argtypes = [C.c_uint32, u32p, u32p, u64p, u64p, u32p, C.c_uint64, u64p, C.c_uint64]
         lib.oracle_ordered.restype = C.c_int
         lib.oracle_ordered.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, u32p, u64p, u64p,
                                        u32p, C.c_uint64, u64p, i32p, C.c_uint64, u64p]
@@ -105,8 +105,9 @@ def _result(stats, hist, n):
             "dead_ends": int(stats[3]), "hash": int(stats[4]), "hist": hist.copy()}
 
 
-def tomita(n: int, uv, listing: bool = False, list_cap: int = 1 << 22):
-    """Maximal cliques by Alg. 2 with the Tomita pivot."""
+def tomita(n: int, uv, listing: bool = False, list_cap: int = 1 << 22, max_nodes: int = 0):
+    """Maximal cliques by Alg. 2 with the Tomita pivot.  ``max_nodes`` > 0
+    stops after that many search nodes (result flagged ``partial``)."""
     lib = _load()
     off, adj = csr(n, uv)
     stats = np.zeros(5, dtype=np.uint64)
@@ -115,13 +116,14 @@ def tomita(n: int, uv, listing: bool = False, list_cap: int = 1 << 22):
     used = np.zeros(1, dtype=np.uint64)
     rc = lib.oracle_tomita(n, _p(off, C.c_uint32), _p(adj if adj.size else np.zeros(1, np.uint32), C.c_uint32),
                            _p(stats, C.c_uint64), _p(hist, C.c_uint64),
-                           _p(lst, C.c_uint32) if listing else None, lst.size, _p(used, C.c_uint64))
-    if rc:
+                           _p(lst, C.c_uint32) if listing else None, lst.size, _p(used, C.c_uint64), max_nodes)
+    if rc < 0:
         raise MemoryError("oracle ran out of memory")
     res = _result(stats, hist, n)
+    res["partial"] = rc == 1
     if listing:
         if int(used[0]) > lst.size:
-            return tomita(n, uv, True, int(used[0]) + 16)
+            return tomita(n, uv, True, int(used[0]) + 16, max_nodes)
         res["listing"] = _unpack_listing(lst, int(used[0]))
     return res
 

@@ -149,7 +149,8 @@ typedef struct {
     int mode;                       /* pivot rule of oracle_ordered          */
     int32_t *trace;                 /* optional: first internal nodes        */
     uint64_t trace_cap, trace_used;
-    int oom;
+    uint64_t max_nodes;             /* 0 = unlimited; else stop after this   */
+    int oom, stopped;
 } run_t;
 
 static uint32_t *level_buf(run_t *r, uint32_t d)
@@ -219,7 +220,8 @@ static const uint32_t *nbr(const run_t *r, uint32_t v, uint32_t *deg)
 
 static void bk_tomita(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t nx, uint32_t rn)
 {
-    if (r->oom) return;
+    if (r->oom || r->stopped) return;
+    if (r->max_nodes && r->nodes >= r->max_nodes) { r->stopped = 1; return; }
     r->nodes++;
     if (np == 0 && nx == 0) { report(r, rn); return; }
     if (np == 0) { r->dead_ends++; return; }
@@ -391,12 +393,16 @@ static void run_stats(const run_t *r, uint64_t *stats, uint64_t *list_used)
     if (list_used) *list_used = r->list_used;
 }
 
+/* max_nodes > 0 stops the enumeration after that many search nodes (a
+ * bounded sample for timing; the counters then cover the part explored) and
+ * the return value is 1. */
 int oracle_tomita(uint32_t n, const uint32_t *off, const uint32_t *adj,
                   uint64_t *stats, uint64_t *hist,
-                  uint32_t *list, uint64_t list_cap, uint64_t *list_used)
+                  uint32_t *list, uint64_t list_cap, uint64_t *list_used, uint64_t max_nodes)
 {
     run_t r;
     int rc = run_init(&r, n, hist, list, list_cap);
+    r.max_nodes = max_nodes;
     uint32_t *ident = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
     uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
     uint32_t *X = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
@@ -404,7 +410,7 @@ int oracle_tomita(uint32_t n, const uint32_t *off, const uint32_t *adj,
     for (uint32_t v = 0; v < n; ++v) { ident[v] = v; P[v] = v; }
     r.off = off; r.adj = adj; r.label = ident;
     bk_tomita(&r, P, n, X, 0, 0);
-    rc = r.oom ? -2 : 0;
+    rc = r.oom ? -2 : (r.stopped ? 1 : 0);
     run_stats(&r, stats, list_used);
 done:
     free(ident); free(P); free(X);

@@ -44,7 +44,7 @@ class MceError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("pivot_mode", C.c_uint32), ("flags", C.c_uint32), ("lanes_per_subtree", C.c_uint32),
                 ("words_per_lane", C.c_uint32), ("blocks", C.c_uint32), ("threads_per_block", C.c_uint32),
-                ("timeout_ns", C.c_uint64), ("stack_levels", C.c_uint32), ("_reserved", C.c_uint32)]
+                ("timeout_ns", C.c_uint64), ("stack_levels", C.c_uint32), ("queue_log2", C.c_uint32)]
 
 
 class Result(C.Structure):
@@ -58,13 +58,13 @@ class Result(C.Structure):
 
 def options(pivot: str | int = "greedy", identity_order: bool = False, lanes: int = 0, words: int = 0,
             blocks: int = 0, threads: int = 0, timeout_ns: int = 0, stack_levels: int = 0,
-            flags: int = 0) -> Options:
+            queue_log2: int = 0, flags: int = 0) -> Options:
     o = Options()
     o.pivot_mode = PIVOTS[pivot] if isinstance(pivot, str) else int(pivot)
     o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0)
     o.lanes_per_subtree, o.words_per_lane = lanes, words
     o.blocks, o.threads_per_block = blocks, threads
-    o.timeout_ns, o.stack_levels = timeout_ns, stack_levels
+    o.timeout_ns, o.stack_levels, o.queue_log2 = timeout_ns, stack_levels, queue_log2
     return o
 
 

@@ -87,7 +87,8 @@ void default_shape(uint32_t n, int &G, int &K)
 
 int choose(uint32_t n, const mce_options &o, Config &c)
 {
-    if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth) return MCE_EINVAL;
+    if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
+        return MCE_EINVAL;
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
     int G, K;
     default_shape(n, G, K);
@@ -127,6 +128,7 @@ int choose(uint32_t n, const mce_options &o, Config &c)
     }
     c.total_groups = c.blocks * (c.threads / 32) * (32 / G);
     c.qcap = next_pow2(std::max<uint64_t>(1024, 2ull * c.total_groups + 256));
+    if (o.queue_log2) c.qcap = std::max<uint32_t>(c.qcap, 1u << o.queue_log2);
     c.fs = (uint32_t)round_up(kFrameHdr + 2 * c.wp, 4);
     return MCE_OK;
 }
@@ -511,13 +513,34 @@ int fill_result(const std::vector<uint64_t> &h, uint32_t n, mce_result *res)
 
 }  // namespace
 
+namespace {
+int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0);
+}
+
 extern "C" int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res)
 {
     if (!g || !res) return MCE_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
+    DevicePick pick(g->ctx->device);
+    mce_options o = defaults(opts);
+    int rc = enumerate_once(g, o, res, t0);
+    // a queue overflow leaves no partial state behind: retry with 16x the slots
+    for (int tries = 0; rc == MCE_EOVERFLOW && tries < 2; ++tries) {
+        Config c;
+        if (choose(g->n, o, c) != MCE_OK) break;
+        uint32_t lg = 0;
+        while ((1u << lg) < c.qcap) ++lg;
+        if (lg + 4 > 24) break;
+        o.queue_log2 = lg + 4;
+        rc = enumerate_once(g, o, res, t0);
+    }
+    return rc;
+}
+
+namespace {
+int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0)
+{
     mce_ctx *ctx = g->ctx;
-    DevicePick pick(ctx->device);
-    const mce_options o = defaults(opts);
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
     uint64_t sbytes = 0;
     int rc = mce_scratch_bytes(g->n, &o, &sbytes);
@@ -556,6 +579,7 @@ extern "C" int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *
     res->total_ms = ms_since(t0);
     return rc;
 }
+}  // namespace
 
 extern "C" int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options *opts,
                                    mce_result *res)
