@@ -194,7 +194,8 @@ def run_ours(args):
 
     uv = synth.gnp(N, P, SEED)
     W = words(N)
-    opts = mce.options()
+    opts = mce.options(lanes=args.lanes, words=args.words, threads=args.threads, blocks=args.blocks,
+                       split_min_p=args.split)
     wp = mce.mce_search_words(N, opts)
     s = torch.cuda.Stream(device=dev)
     rows = torch.from_numpy(synth.to_bitset(N, uv).view(np.int32).reshape(-1)).to(dev)
@@ -339,6 +340,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    # launch-shape overrides (0 = the library's choice)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--words", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--blocks", type=int, default=0)
+    ap.add_argument("--split", type=int, default=0)
     args = ap.parse_args()
     select_workload(args.workload)
     if args.warmup < 3 and args.impl == "ours":

@@ -103,9 +103,18 @@ typedef struct {
                                    frames spill to the device work queue,
                                    1..64; 0 = 64                              */
     uint32_t queue_log2;        /* log2 of the device work-queue slots, <= 24;
-                                   0 = auto (at least twice the subtree
+                                   0 = auto (at least four times the subtree
                                    groups).  mce_enumerate retries a search
                                    that overflowed with a 16x larger queue.   */
+    uint32_t split_min_p;       /* a new subtree whose candidate set P has at
+                                   least this many vertices is published to
+                                   the device work queue (breadth-first
+                                   split of the top of the search tree) while
+                                   the queue holds fewer than half its slots;
+                                   0 = by edge density (about 64 expected
+                                   maximal cliques in such a subtree),
+                                   0xffffffff = never                      */
+    uint32_t _reserved;
 } mce_options;
 
 /* Layout of the device result array d_out (uint64 words, zeroed and filled
@@ -118,6 +127,7 @@ typedef struct {
 #define MCE_OUT_STATUS     5   /* 0 or a negative MCE_* code (as int64)      */
 #define MCE_OUT_MAX_SIZE   6   /* size of the largest maximal clique         */
 #define MCE_OUT_DONATIONS  7   /* work frames handed between warps           */
+#define MCE_OUT_STEALS     8   /* frames taken from the work queue           */
 #define MCE_OUT_HIST       16
 #define MCE_OUT_WORDS(n)   (MCE_OUT_HIST + (uint64_t)(n) + 1)
 
@@ -215,6 +225,9 @@ void mce_ctx_destroy(mce_ctx *ctx);
 int mce_load_edges(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint64_t m, mce_graph **out);
 int mce_load_bitset(mce_ctx *ctx, uint32_t n, const uint32_t *rows, uint32_t words_per_row,
                     mce_graph **out);
+/* Release a graph.  Free every graph (and batch) of a context before
+ * destroying the context; a graph must not be freed while a request or batch
+ * that uses it is still running. */
 void mce_graph_free(mce_graph *g);
 
 /* Enumerate one graph (plain form).  `res` is in/out: hist and list buffers
@@ -222,8 +235,27 @@ void mce_graph_free(mce_graph *g);
  * max_size or the listing does not fit (counters still valid). */
 int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
 
-/* Enumerate `count` graphs in one persistent launch (batched form);
- * res[i] belongs to graphs[i]. */
+/* Batched form.  mce_batch_create plans a batch of loaded graphs once:
+ * graphs are grouped by subtree shape (lanes x words, chosen per graph like
+ * mce_enumerate does, or forced by opts), ordered most expensive first by the
+ * expected number of maximal cliques of G(n, m / C(n, 2)), and the whole
+ * pipeline (ordering, renumbering, one persistent search launch per shape,
+ * each block taking one graph at a time) is captured into a CUDA graph.
+ * mce_batch_launch enqueues that graph on the context stream;
+ * mce_batch_results waits and fills res[i] for graphs[i] (hist buffers
+ * caller-owned as in mce_enumerate); mce_batch_run does both.  The graphs
+ * must stay loaded while the batch exists.  Returns the first per-graph
+ * error, with every res[i].status filled. */
+typedef struct mce_batch mce_batch;
+int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
+                     const mce_options *opts, mce_batch **out);
+int mce_batch_launch(mce_batch *b);
+int mce_batch_results(mce_batch *b, mce_result *res);
+int mce_batch_run(mce_batch *b, mce_result *res);
+void mce_batch_destroy(mce_batch *b);
+
+/* create + run + destroy: `count` graphs in one captured launch; res[i]
+ * belongs to graphs[i]. */
 int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
                         const mce_options *opts, mce_result *res);
 

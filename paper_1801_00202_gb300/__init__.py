@@ -28,6 +28,7 @@ MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED = 0x1, 0x2, 0x4
 
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
 MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
+MCE_OUT_STEALS = 8
 MCE_OUT_HIST = 16
 
 
@@ -44,7 +45,8 @@ class MceError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("pivot_mode", C.c_uint32), ("flags", C.c_uint32), ("lanes_per_subtree", C.c_uint32),
                 ("words_per_lane", C.c_uint32), ("blocks", C.c_uint32), ("threads_per_block", C.c_uint32),
-                ("timeout_ns", C.c_uint64), ("stack_levels", C.c_uint32), ("queue_log2", C.c_uint32)]
+                ("timeout_ns", C.c_uint64), ("stack_levels", C.c_uint32), ("queue_log2", C.c_uint32),
+                ("split_min_p", C.c_uint32), ("_reserved", C.c_uint32)]
 
 
 class Result(C.Structure):
@@ -58,13 +60,14 @@ class Result(C.Structure):
 
 def options(pivot: str | int = "greedy", identity_order: bool = False, lanes: int = 0, words: int = 0,
             blocks: int = 0, threads: int = 0, timeout_ns: int = 0, stack_levels: int = 0,
-            queue_log2: int = 0, flags: int = 0) -> Options:
+            queue_log2: int = 0, split_min_p: int = 0, flags: int = 0) -> Options:
     o = Options()
     o.pivot_mode = PIVOTS[pivot] if isinstance(pivot, str) else int(pivot)
     o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0)
     o.lanes_per_subtree, o.words_per_lane = lanes, words
     o.blocks, o.threads_per_block = blocks, threads
     o.timeout_ns, o.stack_levels, o.queue_log2 = timeout_ns, stack_levels, queue_log2
+    o.split_min_p = split_min_p
     return o
 
 
@@ -87,6 +90,11 @@ _SIGS = {
     "mce_graph_free": (None, [_VP]),
     "mce_enumerate": (C.c_int, [_VP, C.POINTER(Options), C.POINTER(Result)]),
     "mce_enumerate_batch": (C.c_int, [_VP, C.POINTER(_VP), _U32, C.POINTER(Options), C.POINTER(Result)]),
+    "mce_batch_create": (C.c_int, [_VP, C.POINTER(_VP), _U32, C.POINTER(Options), C.POINTER(_VP)]),
+    "mce_batch_launch": (C.c_int, [_VP]),
+    "mce_batch_results": (C.c_int, [_VP, C.POINTER(Result)]),
+    "mce_batch_run": (C.c_int, [_VP, C.POINTER(Result)]),
+    "mce_batch_destroy": (None, [_VP]),
     "mce_submit": (C.c_int, [_VP, _VP, C.POINTER(Options), C.POINTER(_U64)]),
     "mce_poll": (C.c_int, [_VP, _U64, C.POINTER(Result)]),
     "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
@@ -188,21 +196,27 @@ def decode_out(out, n: int) -> dict:
             "internal": int(a[MCE_OUT_INTERNAL]), "dead_ends": int(a[MCE_OUT_DEAD_ENDS]),
             "hash": int(a[MCE_OUT_HASH]), "status": int(a[MCE_OUT_STATUS].astype(np.int64)),
             "max_size": int(a[MCE_OUT_MAX_SIZE]), "donations": int(a[MCE_OUT_DONATIONS]),
+            "steals": int(a[MCE_OUT_STEALS]),
             "hist": a[MCE_OUT_HIST:MCE_OUT_HIST + n + 1].copy()}
 
 
 # --- handle API -------------------------------------------------------------
 
 class Context:
-    """mce_ctx: a device, a stream and a device-memory budget."""
+    """mce_ctx: a device, a stream and a device-memory budget.  Graphs and
+    batches made from a context are released before it is destroyed."""
 
     def __init__(self, device: int = 0, mem_budget: int = 0, stream=None):
+        import weakref
         h = C.c_void_p()
         _check(lib().mce_ctx_create(device, mem_budget, _stream(stream), C.byref(h)), "mce_ctx_create")
         self.handle = h
+        self._owned = weakref.WeakSet()
 
     def close(self):
         if self.handle:
+            for obj in list(self._owned):
+                obj.close()
             lib().mce_ctx_destroy(self.handle)
             self.handle = None
 
@@ -219,7 +233,43 @@ class Context:
         h = C.c_void_p()
         _check(lib().mce_load_edges(self.handle, n, uv.ctypes.data if uv.size else None, uv.shape[0], C.byref(h)),
                "mce_load_edges")
-        return Graph(self, h, n)
+        g = Graph(self, h, n)
+        self._owned.add(g)
+        return g
+
+    # --- served form ------------------------------------------------------
+    def submit(self, graph: "Graph", opts: Options | None = None) -> int:
+        t = C.c_uint64(0)
+        _check(lib().mce_submit(self.handle, graph.handle, _opt(opts), C.byref(t)), "mce_submit")
+        if not hasattr(self, "_tickets"):
+            self._tickets = {}
+        self._tickets[int(t.value)] = graph.n
+        return int(t.value)
+
+    def _collect(self, ticket: int, call, *extra):
+        n = self._tickets[ticket]
+        hist = np.zeros(n + 1, dtype=np.uint64)
+        r = Result()
+        r.hist = hist.ctypes.data_as(C.POINTER(C.c_uint64))
+        r.hist_cap = hist.size
+        rc = call(self.handle, ticket, *extra, C.byref(r))
+        if rc == MCE_PENDING or rc == MCE_ETIMEOUT:
+            return rc, None
+        del self._tickets[ticket]
+        return rc, {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
+                    "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
+                    "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}
+
+    def poll(self, ticket: int):
+        """mce_poll: None while pending, else the result dict (rc inside)."""
+        rc, res = self._collect(ticket, lib().mce_poll)
+        return res
+
+    def wait(self, ticket: int, timeout_ns: int = 0):
+        rc, res = self._collect(ticket, lib().mce_wait, timeout_ns)
+        if res is None:
+            raise MceError(rc, "mce_wait")
+        return res
 
     def load_bitset(self, n: int, rows) -> "Graph":
         rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32))
@@ -227,7 +277,9 @@ class Context:
         h = C.c_void_p()
         _check(lib().mce_load_bitset(self.handle, n, rows.ctypes.data if rows.size else None, w, C.byref(h)),
                "mce_load_bitset")
-        return Graph(self, h, n)
+        g = Graph(self, h, n)
+        self._owned.add(g)
+        return g
 
 
 class Graph:
@@ -238,9 +290,11 @@ class Graph:
 
     def free(self):
         if self.handle:
-            lib().mce_graph_free(self.handle)
+            if self.ctx.handle:
+                lib().mce_graph_free(self.handle)
             self.handle = None
 
+    close = free
     __del__ = free
 
     def enumerate(self, opts: Options | None = None, raise_on_error: bool = True) -> dict:
@@ -254,3 +308,68 @@ class Graph:
         return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
                 "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
                 "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}
+
+
+def _results_array(ns):
+    res = (Result * max(len(ns), 1))()
+    hists = []
+    for i, n in enumerate(ns):
+        h = np.zeros(n + 1, dtype=np.uint64)
+        hists.append(h)
+        res[i].hist = h.ctypes.data_as(C.POINTER(C.c_uint64))
+        res[i].hist_cap = h.size
+    return res, hists
+
+
+def _result_dicts(res, hists):
+    out = []
+    for i, h in enumerate(hists):
+        r = res[i]
+        out.append({"status": int(C.c_int32(r.status).value), "count": r.count, "nodes": r.nodes,
+                    "internal": r.internal_nodes, "dead_ends": r.dead_ends, "hash": r.hash,
+                    "max_size": r.max_size, "hist": h, "kernel_ms": r.kernel_ms})
+    return out
+
+
+class Batch:
+    """mce_batch: graphs planned once and captured into one CUDA graph."""
+
+    def __init__(self, ctx: Context, graphs, opts: Options | None = None):
+        self.ctx, self.graphs = ctx, list(graphs)
+        arr = (C.c_void_p * max(len(self.graphs), 1))(*[g.handle for g in self.graphs])
+        h = C.c_void_p()
+        _check(lib().mce_batch_create(ctx.handle, arr, len(self.graphs), _opt(opts), C.byref(h)), "mce_batch_create")
+        self.handle = h
+        ctx._owned.add(self)
+        self._res, self._hists = _results_array([g.n for g in self.graphs])
+
+    def launch(self):
+        _check(lib().mce_batch_launch(self.handle), "mce_batch_launch")
+
+    def results(self, raise_on_error: bool = True):
+        rc = lib().mce_batch_results(self.handle, self._res)
+        if raise_on_error:
+            _check(rc, "mce_batch_results")
+        return _result_dicts(self._res, [h.copy() for h in self._hists])
+
+    def run(self, raise_on_error: bool = True):
+        self.launch()
+        return self.results(raise_on_error)
+
+    def close(self):
+        if self.handle:
+            if self.ctx.handle:
+                lib().mce_batch_destroy(self.handle)
+            self.handle = None
+
+    __del__ = close
+
+
+def enumerate_batch(ctx: Context, graphs, opts: Options | None = None):
+    """mce_enumerate_batch: create, run and destroy a batch in one call."""
+    graphs = list(graphs)
+    arr = (C.c_void_p * max(len(graphs), 1))(*[g.handle for g in graphs])
+    res, hists = _results_array([g.n for g in graphs])
+    rc = lib().mce_enumerate_batch(ctx.handle, arr, len(graphs), _opt(opts), res)
+    _check(rc, "mce_enumerate_batch")
+    return _result_dicts(res, hists)

@@ -1,7 +1,14 @@
 // C ABI of libmce (include/mce.h): launch configuration, scratch layout,
 // device-level step calls and the host-level handle API.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -24,7 +31,7 @@ struct Config {
     uint32_t qcap = 1024, fs = 0;
     uint32_t total_groups = 0;
     int pivot = 0;
-    SearchImpl impl{nullptr, nullptr};
+    SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
 };
 
 struct Layout {
@@ -54,7 +61,7 @@ SearchImpl impl_for(int G, int K, bool smem, int pivot)
     case 32 * 8 + 1: return search_impl_32_1(smem, pivot);
     case 32 * 8 + 2: return search_impl_32_2(smem, pivot);
     case 32 * 8 + 4: return search_impl_32_4(smem, pivot);
-    default: return {nullptr, nullptr};
+    default: return {nullptr, nullptr, nullptr, nullptr};
     }
 }
 
@@ -65,10 +72,7 @@ uint32_t next_pow2(uint64_t x)
     return (uint32_t)p;
 }
 
-size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem)
-{
-    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + ((size_t)n + 1) * 4;
-}
+size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem) { return search_smem_bytes(n, wp, rows_in_smem); }
 
 // Default subtree width: the narrowest group whose sets still fit one word
 // per lane, one thread per subtree below 65 vertices.
@@ -127,9 +131,9 @@ int choose(uint32_t n, const mce_options &o, Config &c)
         c.blocks = (unsigned)(per_sm * sms);
     }
     c.total_groups = c.blocks * (c.threads / 32) * (32 / G);
-    c.qcap = next_pow2(std::max<uint64_t>(1024, 2ull * c.total_groups + 256));
+    c.qcap = next_pow2(std::max<uint64_t>(1024, 4ull * c.total_groups + 256));
     if (o.queue_log2) c.qcap = std::max<uint32_t>(c.qcap, 1u << o.queue_log2);
-    c.fs = (uint32_t)round_up(kFrameHdr + 2 * c.wp, 4);
+    c.fs = (uint32_t)frame_words(c.wp);
     return MCE_OK;
 }
 
@@ -171,6 +175,8 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
     p.total_groups = c.total_groups;
     p.pivot_mode = (uint32_t)c.pivot;
     p.stack_levels = o.stack_levels ? std::min<uint32_t>(o.stack_levels, kStackDepth) : kStackDepth;
+    p.split_min_p = o.split_min_p;  // 0: by density
+    p.split_target = c.qcap / 2;
     return p;
 }
 
@@ -278,13 +284,16 @@ extern "C" int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const ui
 // ---------------------------------------------------------------------------
 // Host-level API
 
+struct Server;
+
 struct mce_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaMemPool_t pool = nullptr;
     uint64_t budget = 0;
-    uint64_t used = 0;
+    std::atomic<uint64_t> used{0};
+    Server *server = nullptr;  // started by the first mce_submit
 };
 
 struct mce_graph {
@@ -292,6 +301,7 @@ struct mce_graph {
     uint32_t n = 0, w = 0;
     uint32_t *d_rows = nullptr;
     uint64_t bytes = 0;
+    uint64_t m = 0;  // edges (as given: an estimate when duplicates were passed)
 };
 
 namespace {
@@ -311,25 +321,29 @@ struct DevicePick {
     }
 };
 
-int dalloc(mce_ctx *ctx, void **p, size_t bytes)
+int dalloc(mce_ctx *ctx, void **p, size_t bytes, cudaStream_t s = nullptr)
 {
     if (bytes == 0) bytes = 256;
-    if (ctx->budget && ctx->used + bytes > ctx->budget) return MCE_ENOMEM;
-    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
+    if (ctx->budget && ctx->used.fetch_add(bytes) + bytes > ctx->budget) {
+        ctx->used.fetch_sub(bytes);
         return MCE_ENOMEM;
     }
-    ctx->used += bytes;
+    if (!ctx->budget) ctx->used.fetch_add(bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s ? s : ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->used.fetch_sub(bytes);
+        return MCE_ENOMEM;
+    }
     return MCE_OK;
 }
 
-void dfree(mce_ctx *ctx, void *p, size_t bytes)
+void dfree(mce_ctx *ctx, void *p, size_t bytes, cudaStream_t s = nullptr)
 {
     if (!p) return;
-    cudaFreeAsync(p, ctx->stream);
+    cudaFreeAsync(p, s ? s : ctx->stream);
     if (bytes == 0) bytes = 256;
-    ctx->used -= std::min<uint64_t>(ctx->used, bytes);
+    ctx->used.fetch_sub(bytes);
 }
 
 double ms_since(std::chrono::steady_clock::time_point t0)
@@ -381,11 +395,14 @@ extern "C" int mce_ctx_create(int device, uint64_t mem_budget_bytes, void *strea
     return MCE_OK;
 }
 
+void server_stop(mce_ctx *ctx);
+
 extern "C" void mce_ctx_destroy(mce_ctx *ctx)
 {
     if (!ctx) return;
     {
         DevicePick pick(ctx->device);
+        server_stop(ctx);
         cudaStreamSynchronize(ctx->stream);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -424,6 +441,7 @@ extern "C" int mce_load_edges(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint
     g->n = n;
     g->w = std::max<uint32_t>(1, (n + 31) / 32);
     g->bytes = (uint64_t)std::max<uint32_t>(n, 1) * g->w * 4;
+    g->m = m;
     uint32_t *d_uv = nullptr;
     uint64_t *d_status = nullptr;
     int rc = dalloc(ctx, (void **)&g->d_rows, g->bytes);
@@ -459,6 +477,8 @@ extern "C" int mce_load_bitset(mce_ctx *ctx, uint32_t n, const uint32_t *rows, u
     g->n = n;
     g->w = std::max<uint32_t>(1, words_per_row);
     g->bytes = (uint64_t)std::max<uint32_t>(n, 1) * g->w * 4;
+    for (uint64_t i = 0; i < (uint64_t)n * words_per_row; ++i) g->m += (uint64_t)__builtin_popcount(rows[i]);
+    g->m /= 2;
     uint64_t *d_status = nullptr;
     int rc = dalloc(ctx, (void **)&g->d_rows, g->bytes);
     if (rc == MCE_OK) rc = dalloc(ctx, (void **)&d_status, 64);
@@ -581,29 +601,597 @@ int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chr
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Batched form
+
+struct mce_batch {
+    mce_ctx *ctx = nullptr;
+    uint32_t count = 0;
+    std::vector<uint32_t> n;
+    std::vector<size_t> out_off;  // words into d_out
+    size_t out_words = 0;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    uint64_t *d_out = nullptr;
+    std::vector<uint64_t> h_out;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> events;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+};
+
+namespace {
+
+// Expected number of maximal cliques of G(n, p) (sum over clique sizes k of
+// C(n,k) p^C(k,2) (1 - p^k)^(n-k)): the cost key that orders a batch.
+double expected_cliques(uint32_t n, uint64_t m)
+{
+    if (n < 2) return 1.0;
+    const double p = std::min(1.0, (double)m / (0.5 * n * (n - 1.0)));
+    if (p <= 0.0) return n;
+    if (p >= 1.0) return 1.0;
+    double total = 0.0;
+    const double ln = std::lgamma(n + 1.0), lp = std::log(p);
+    for (uint32_t k = 1; k <= n; ++k) {
+        const double t = ln - std::lgamma(k + 1.0) - std::lgamma(n - k + 1.0) + 0.5 * k * (k - 1.0) * lp +
+                         (n - k) * std::log1p(-std::pow(p, (double)k));
+        total += std::exp(t);
+    }
+    return total + n;
+}
+
+struct Bucket {
+    int G = 0, K = 0;
+    bool smem = false;
+    std::vector<uint32_t> graphs;
+    SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
+    LaunchShape shape{};
+    uint32_t qcap = 0, fs = 0, groups = 0;
+    size_t qstride = 0, list_off = 0, region_off = 0, next_off = 0;
+};
+
+void batch_free(mce_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->dmem) dfree(b->ctx, b->dmem, b->dbytes);
+    cudaStreamSynchronize(b->ctx->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options *opts,
+                                mce_batch **out)
+{
+    if (!ctx || !out || (count && !graphs) || count > 65535u) return MCE_EINVAL;
+    *out = nullptr;
+    DevicePick pick(ctx->device);
+    const mce_options o = defaults(opts);
+    if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
+        return MCE_EINVAL;
+    if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+        return MCE_ECUDA;
+
+    mce_batch *b = new (std::nothrow) mce_batch;
+    if (!b) return MCE_ENOMEM;
+    b->ctx = ctx;
+    b->count = count;
+    b->n.resize(count);
+
+    // ---- plan: shape buckets, most expensive graph first
+    std::vector<Bucket> buckets;
+    std::vector<double> cost(count);
+    uint32_t max_n = 0, max_w = 0, max_wp = 0;
+    std::vector<uint32_t> wp_of(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        const mce_graph *g = graphs[i];
+        if (!g || g->ctx != ctx) { delete b; return MCE_EINVAL; }
+        b->n[i] = g->n;
+        const uint32_t W = std::max<uint32_t>(1, (g->n + 31) / 32);
+        int G, K;
+        default_shape(g->n, G, K);
+        if (o.lanes_per_subtree || o.words_per_lane) {
+            if (o.lanes_per_subtree) G = (int)o.lanes_per_subtree;
+            K = o.words_per_lane ? (int)o.words_per_lane : (int)std::max<uint32_t>(1, (W + G - 1) / G);
+            if (K == 3) K = 4;
+        }
+        if ((uint32_t)(G * K) < W || !impl_for(G, K, false, (int)o.pivot_mode).run) { delete b; return MCE_EINVAL; }
+        size_t bi = 0;
+        while (bi < buckets.size() && !(buckets[bi].G == G && buckets[bi].K == K)) ++bi;
+        if (bi == buckets.size()) {
+            Bucket nb;
+            nb.G = G;
+            nb.K = K;
+            nb.smem = G * K <= 32;
+            buckets.push_back(nb);
+        }
+        buckets[bi].graphs.push_back(i);
+        cost[i] = expected_cliques(g->n, g->m);
+        wp_of[i] = (uint32_t)(G * K);
+        max_n = std::max(max_n, g->n);
+        max_w = std::max(max_w, g->w);
+        max_wp = std::max(max_wp, wp_of[i]);
+    }
+
+    // ---- launch shapes and the device memory layout
+    size_t off = 0;
+    auto take = [&](size_t bytes, size_t align) {
+        off = round_up(off, align);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t table_off = take(sizeof(BatchGraph) * std::max<uint32_t>(count, 1), 256);
+    std::vector<size_t> order_off(count), ren_off(count);
+    b->out_off.resize(count);
+    for (uint32_t i = 0; i < count; ++i) order_off[i] = take((size_t)std::max<uint32_t>(b->n[i], 1) * 4, 16);
+    for (uint32_t i = 0; i < count; ++i) ren_off[i] = take((size_t)b->n[i] * wp_of[i] * 4 + 16, 256);
+    const size_t out_at = take(0, 256);
+    for (uint32_t i = 0; i < count; ++i) {
+        b->out_off[i] = b->out_words;
+        b->out_words += MCE_OUT_WORDS(b->n[i]);
+    }
+    off += b->out_words * 8;
+    int rc = MCE_OK;
+    for (Bucket &bk : buckets) {
+        std::stable_sort(bk.graphs.begin(), bk.graphs.end(), [&](uint32_t a, uint32_t c2) { return cost[a] > cost[c2]; });
+        bk.impl = impl_for(bk.G, bk.K, bk.smem, (int)o.pivot_mode);
+        size_t smem = 0;
+        for (uint32_t i : bk.graphs) smem = std::max(smem, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
+        unsigned threads = o.threads_per_block ? o.threads_per_block : 256u;
+        if (threads % 32 || threads > (bk.K >= 4 ? 512u : 1024u)) { rc = MCE_EINVAL; break; }
+        int per_sm = 0;
+        if (bk.impl.batch_occupancy((int)threads, smem, &per_sm) != cudaSuccess || per_sm < 1) { rc = MCE_EINVAL; break; }
+        unsigned blocks = o.blocks ? o.blocks : (unsigned)(per_sm * sms);
+        blocks = std::min<unsigned>(blocks, (unsigned)bk.graphs.size());
+        bk.shape = LaunchShape{blocks, threads, smem, bk.smem};
+        bk.groups = threads / 32 * (32 / bk.G);
+        bk.qcap = next_pow2(std::max<uint64_t>(256, 4ull * bk.groups + 64));
+        if (o.queue_log2) bk.qcap = std::max<uint32_t>(bk.qcap, 1u << o.queue_log2);
+        bk.fs = (uint32_t)frame_words((uint32_t)(bk.G * bk.K));
+        bk.qstride = batch_region_bytes(bk.qcap, bk.fs);
+        bk.list_off = take(bk.graphs.size() * 4, 16);
+        bk.next_off = take(4, 128);
+        bk.region_off = take(bk.qstride * blocks, 256);
+    }
+    if (rc != MCE_OK) { delete b; return rc; }
+    b->dbytes = round_up(off, 256);
+    rc = dalloc(ctx, &b->dmem, b->dbytes);
+    if (rc != MCE_OK) { delete b; return rc; }
+    unsigned char *base = static_cast<unsigned char *>(b->dmem);
+    b->d_out = reinterpret_cast<uint64_t *>(base + out_at);
+
+    // ---- tables
+    std::vector<BatchGraph> table(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        BatchGraph &t = table[i];
+        t.rows = graphs[i]->d_rows;
+        t.order = reinterpret_cast<uint32_t *>(base + order_off[i]);
+        t.ren = reinterpret_cast<uint32_t *>(base + ren_off[i]);
+        t.out = b->d_out + b->out_off[i];
+        t.n = b->n[i];
+        t.w = graphs[i]->w;
+        t.wp = wp_of[i];
+        t.pad = 0;
+    }
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    if (count) e = cudaMemcpyAsync(base + table_off, table.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s);
+    for (const Bucket &bk : buckets)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + bk.list_off, bk.graphs.data(), bk.graphs.size() * 4, cudaMemcpyHostToDevice, s);
+    size_t order_smem = 0;
+    if (e == cudaSuccess) e = prepare_order_batch(max_n, max_w, &order_smem);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (size_t i = 0; e == cudaSuccess && i < buckets.size(); ++i) {
+        cudaStream_t ss = nullptr;
+        e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->side.push_back(ss);
+    }
+    for (size_t i = 0; e == cudaSuccess && i < buckets.size() + 1; ++i) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+
+    // ---- capture: clear results, order, renumber, then one persistent
+    // search launch per shape, forked so their tails overlap
+    const BatchGraph *d_table = reinterpret_cast<const BatchGraph *>(base + table_off);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ce = cudaMemsetAsync(b->d_out, 0, b->out_words * 8, s);
+        for (const Bucket &bk : buckets)
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(base + bk.next_off, 0, 4, s);
+        if (ce == cudaSuccess) ce = launch_order_batch(d_table, count, max_n, order_smem, s);
+        if (ce == cudaSuccess) ce = launch_renumber_batch(d_table, count, max_n, max_wp, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(b->events[0], s);
+        for (size_t i = 0; ce == cudaSuccess && i < buckets.size(); ++i) {
+            const Bucket &bk = buckets[i];
+            BatchParams bp{};
+            bp.graphs = d_table;
+            bp.list = reinterpret_cast<const uint32_t *>(base + bk.list_off);
+            bp.count = (uint32_t)bk.graphs.size();
+            bp.next = reinterpret_cast<unsigned *>(base + bk.next_off);
+            bp.qbase = base + bk.region_off;
+            bp.qstride = bk.qstride;
+            bp.qcap = bk.qcap;
+            bp.fs = bk.fs;
+            bp.timeout_ns = o.timeout_ns ? o.timeout_ns : 60ull * 1000000000ull;
+            bp.pivot_mode = o.pivot_mode;
+            bp.stack_levels = o.stack_levels ? std::min<uint32_t>(o.stack_levels, kStackDepth) : kStackDepth;
+            bp.groups_per_block = bk.groups;
+            bp.split_min_p = o.split_min_p;
+            bp.split_target = bk.qcap / 2;
+            ce = cudaStreamWaitEvent(b->side[i], b->events[0], 0);
+            if (ce == cudaSuccess) ce = bk.impl.run_batch(bp, bk.shape, b->side[i]);
+            if (ce == cudaSuccess) ce = cudaEventRecord(b->events[i + 1], b->side[i]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, b->events[i + 1], 0);
+        }
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamEndCapture(s, &gr);
+        if (e == cudaSuccess) e = ce;
+        b->graph = gr;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return MCE_ECUDA;
+    }
+    b->h_out.assign(b->out_words, 0);
+    *out = b;
+    return MCE_OK;
+}
+
+extern "C" int mce_batch_launch(mce_batch *b)
+{
+    if (!b) return MCE_EINVAL;
+    DevicePick pick(b->ctx->device);
+    cudaError_t e = cudaEventRecord(b->t0, b->ctx->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->ctx->stream);
+    return cuda_code(e);
+}
+
+extern "C" int mce_batch_results(mce_batch *b, mce_result *res)
+{
+    if (!b) return MCE_EINVAL;
+    DevicePick pick(b->ctx->device);
+    cudaError_t e = cudaMemcpyAsync(b->h_out.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, b->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
+    if (e != cudaSuccess) return MCE_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->t0, b->t1);
+    int first = MCE_OK;
+    for (uint32_t i = 0; i < b->count; ++i) {
+        std::vector<uint64_t> h(b->h_out.begin() + (long)b->out_off[i],
+                                b->h_out.begin() + (long)(b->out_off[i] + MCE_OUT_WORDS(b->n[i])));
+        int rc = MCE_OK;
+        if (res) {
+            rc = fill_result(h, b->n[i], &res[i]);
+            res[i].kernel_ms = ms;
+            res[i].total_ms = ms;
+        } else {
+            rc = (int)(int64_t)h[MCE_OUT_STATUS];
+        }
+        if (rc != MCE_OK && first == MCE_OK) first = rc;
+    }
+    return first;
+}
+
+extern "C" int mce_batch_run(mce_batch *b, mce_result *res)
+{
+    int rc = mce_batch_launch(b);
+    return rc != MCE_OK ? rc : mce_batch_results(b, res);
+}
+
+extern "C" void mce_batch_destroy(mce_batch *b)
+{
+    if (!b) return;
+    DevicePick pick(b->ctx->device);
+    batch_free(b);
+}
+
 extern "C" int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options *opts,
                                    mce_result *res)
 {
-    (void)ctx; (void)graphs; (void)count; (void)opts; (void)res;
-    return MCE_ENOTIMPL;
+    mce_batch *b = nullptr;
+    int rc = mce_batch_create(ctx, graphs, count, opts, &b);
+    if (rc != MCE_OK) return rc;
+    rc = mce_batch_run(b, res);
+    mce_batch_destroy(b);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Served form: continuous batching.  A scheduler thread per context admits
+// submitted requests in arrival order while device memory (rows already
+// resident + scratch: work queue and stack space + result) fits the
+// context's budget and a stream slot is free, launches each admitted request's
+// whole path on its own stream with a grid sized by its expected cost, so
+// requests that arrive while others run overlap with them on the device, and
+// retires them as their completion events fire.
+
+namespace {
+
+constexpr int kServeSlots = 48;
+constexpr double kCliquesPerBlock = 20000.0;
+
+struct Request {
+    mce_ticket id = 0;
+    mce_graph *g = nullptr;
+    mce_options o{};
+    uint64_t scratch_bytes = 0, out_bytes = 0, need = 0;
+    void *scratch = nullptr;
+    uint64_t *d_out = nullptr;
+    int slot = -1;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int rc = MCE_OK;
+    std::vector<uint64_t> words;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    float kernel_ms = 0.f;
+};
+
+}  // namespace
+
+struct Server {
+    mce_ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<Request *> pending;
+    std::vector<Request *> running;
+    std::unordered_map<mce_ticket, Request *> all;
+    std::thread th;
+    bool stop = false;
+    mce_ticket next = 1;
+    uint64_t in_use = 0;
+    int sms = 1;
+    cudaStream_t streams[kServeSlots] = {};
+    cudaEvent_t ev0[kServeSlots] = {}, ev1[kServeSlots] = {};
+    uint64_t *pinned[kServeSlots] = {};
+    bool busy[kServeSlots] = {};
+};
+
+namespace {
+
+void retire(Server *sv, Request *r, int rc)
+{
+    const int i = r->slot;
+    if (rc == MCE_OK) {
+        r->words.assign(sv->pinned[i], sv->pinned[i] + MCE_OUT_WORDS(r->g->n));
+        cudaEventElapsedTime(&r->kernel_ms, sv->ev0[i], sv->ev1[i]);
+    }
+    r->rc = rc;
+    dfree(sv->ctx, r->scratch, r->scratch_bytes, sv->streams[i]);
+    dfree(sv->ctx, r->d_out, r->out_bytes, sv->streams[i]);
+    sv->in_use -= r->need;
+    sv->busy[i] = false;
+    r->slot = -1;
+    r->state = 2;
+    r->t_done = std::chrono::steady_clock::now();
+}
+
+// Launch one request on a free slot; false when it must wait.
+bool admit(Server *sv, Request *r)
+{
+    int slot = -1;
+    for (int i = 0; i < kServeSlots; ++i)
+        if (!sv->busy[i]) { slot = i; break; }
+    if (slot < 0) return false;
+    if (sv->ctx->budget && sv->in_use + r->need > sv->ctx->budget) return false;
+    cudaStream_t s = sv->streams[slot];
+    int rc = dalloc(sv->ctx, &r->scratch, r->scratch_bytes, s);
+    if (rc == MCE_OK) rc = dalloc(sv->ctx, (void **)&r->d_out, r->out_bytes, s);
+    if (rc == MCE_ENOMEM) {
+        dfree(sv->ctx, r->scratch, r->scratch_bytes, s);
+        r->scratch = nullptr;
+        return false;  // retry once others have retired
+    }
+    sv->busy[slot] = true;
+    r->slot = slot;
+    sv->in_use += r->need;
+    cudaError_t e = cudaEventRecord(sv->ev0[slot], s);
+    if (e == cudaSuccess) {
+        rc = mce_enumerate_device(r->g->n, r->g->w, r->g->d_rows, &r->o, r->scratch, r->scratch_bytes, r->d_out, s);
+        if (rc == MCE_OK)
+            e = cudaMemcpyAsync(sv->pinned[slot], r->d_out, r->out_bytes, cudaMemcpyDeviceToHost, s);
+        if (rc == MCE_OK && e == cudaSuccess) e = cudaEventRecord(sv->ev1[slot], s);
+    }
+    if (rc == MCE_OK && e != cudaSuccess) rc = MCE_ECUDA;
+    r->state = 1;
+    if (rc != MCE_OK) {
+        cudaStreamSynchronize(s);
+        retire(sv, r, rc);
+        sv->done_cv.notify_all();
+        return true;
+    }
+    sv->running.push_back(r);
+    return true;
+}
+
+void serve_loop(Server *sv)
+{
+    DevicePick pick(sv->ctx->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (!sv->stop) {
+        bool changed = false;
+        for (size_t k = 0; k < sv->running.size();) {
+            Request *r = sv->running[k];
+            const cudaError_t q = cudaEventQuery(sv->ev1[r->slot]);
+            if (q == cudaErrorNotReady) { ++k; continue; }
+            retire(sv, r, q == cudaSuccess ? MCE_OK : MCE_ECUDA);
+            sv->running[k] = sv->running.back();
+            sv->running.pop_back();
+            changed = true;
+        }
+        while (!sv->pending.empty()) {
+            Request *r = sv->pending.front();
+            if (r->need > sv->ctx->budget && sv->ctx->budget) {  // can never fit
+                sv->pending.pop_front();
+                r->rc = MCE_ENOMEM;
+                r->state = 2;
+                r->t_done = std::chrono::steady_clock::now();
+                changed = true;
+                continue;
+            }
+            if (!admit(sv, r)) break;
+            sv->pending.pop_front();
+            changed = true;
+        }
+        if (changed) sv->done_cv.notify_all();
+        if (sv->running.empty() && sv->pending.empty()) {
+            sv->cv.wait(lk);
+        } else {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+}
+
+int server_start(mce_ctx *ctx)
+{
+    Server *sv = new (std::nothrow) Server;
+    if (!sv) return MCE_ENOMEM;
+    sv->ctx = ctx;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kServeSlots && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&sv->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&sv->ev0[i]);
+        if (e == cudaSuccess) e = cudaEventCreate(&sv->ev1[i]);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sv->pinned[i], MCE_OUT_WORDS(MCE_NMAX) * 8);
+    }
+    if (e != cudaSuccess) {
+        for (int i = 0; i < kServeSlots; ++i) {
+            if (sv->streams[i]) cudaStreamDestroy(sv->streams[i]);
+            if (sv->ev0[i]) cudaEventDestroy(sv->ev0[i]);
+            if (sv->ev1[i]) cudaEventDestroy(sv->ev1[i]);
+            if (sv->pinned[i]) cudaFreeHost(sv->pinned[i]);
+        }
+        delete sv;
+        return MCE_ECUDA;
+    }
+    sv->th = std::thread(serve_loop, sv);
+    ctx->server = sv;
+    return MCE_OK;
+}
+
+}  // namespace
+
+void server_stop(mce_ctx *ctx)
+{
+    Server *sv = ctx->server;
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    sv->th.join();
+    for (int i = 0; i < kServeSlots; ++i) cudaStreamSynchronize(sv->streams[i]);
+    for (Request *r : sv->running) retire(sv, r, MCE_ECUDA);
+    for (auto &kv : sv->all) delete kv.second;
+    for (int i = 0; i < kServeSlots; ++i) {
+        cudaStreamDestroy(sv->streams[i]);
+        cudaEventDestroy(sv->ev0[i]);
+        cudaEventDestroy(sv->ev1[i]);
+        cudaFreeHost(sv->pinned[i]);
+    }
+    delete sv;
+    ctx->server = nullptr;
 }
 
 extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out)
 {
-    (void)ctx; (void)g; (void)opts; (void)out;
-    return MCE_ENOTIMPL;
+    if (!ctx || !g || !out || g->ctx != ctx) return MCE_EINVAL;
+    DevicePick pick(ctx->device);
+    mce_options o = defaults(opts);
+    if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
+    if (!ctx->server) {
+        int rc = server_start(ctx);
+        if (rc) return rc;
+    }
+    Server *sv = ctx->server;
+    if (!o.threads_per_block) o.threads_per_block = 256;
+    if (!o.blocks) {
+        const double cost = expected_cliques(g->n, g->m);
+        o.blocks = (uint32_t)std::min<double>(std::max(1.0, std::ceil(cost / kCliquesPerBlock)), 4.0 * sv->sms);
+    }
+    Request *r = new (std::nothrow) Request;
+    if (!r) return MCE_ENOMEM;
+    r->g = g;
+    r->o = o;
+    int rc = mce_scratch_bytes(g->n, &o, &r->scratch_bytes);
+    if (rc) { delete r; return rc; }
+    r->out_bytes = MCE_OUT_WORDS(g->n) * 8;
+    r->need = r->scratch_bytes + r->out_bytes;
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->id = sv->next++;
+        sv->all[r->id] = r;
+        sv->pending.push_back(r);
+    }
+    sv->cv.notify_all();
+    *out = r->id;
+    return MCE_OK;
 }
+
+namespace {
+
+// Caller holds the lock; the request is done.  Fills res and forgets it.
+int deliver(Server *sv, Request *r, mce_result *res)
+{
+    int rc = r->rc;
+    if (rc == MCE_OK) {
+        rc = fill_result(r->words, r->g->n, res);
+        res->kernel_ms = r->kernel_ms;
+    } else {
+        res->status = (uint32_t)rc;
+    }
+    res->total_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    sv->all.erase(r->id);
+    delete r;
+    return rc;
+}
+
+}  // namespace
 
 extern "C" int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res)
 {
-    (void)ctx; (void)t; (void)res;
-    return MCE_ENOTIMPL;
+    if (!ctx || !res || !ctx->server) return MCE_EINVAL;
+    Server *sv = ctx->server;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(t);
+    if (it == sv->all.end()) return MCE_EINVAL;
+    if (it->second->state != 2) return MCE_PENDING;
+    return deliver(sv, it->second, res);
 }
 
 extern "C" int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res)
 {
-    (void)ctx; (void)t; (void)timeout_ns; (void)res;
-    return MCE_ENOTIMPL;
+    if (!ctx || !res || !ctx->server) return MCE_EINVAL;
+    Server *sv = ctx->server;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(t);
+    if (it == sv->all.end()) return MCE_EINVAL;
+    Request *r = it->second;
+    const auto limit = std::chrono::nanoseconds(timeout_ns ? timeout_ns : 3600ull * 1000000000ull);
+    if (!sv->done_cv.wait_for(lk, limit, [&] { return r->state == 2; })) return MCE_ETIMEOUT;
+    return deliver(sv, r, res);
 }
 
 extern "C" const char *mce_strerror(int code)

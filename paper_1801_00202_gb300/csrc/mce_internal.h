@@ -24,12 +24,35 @@ constexpr int kStackDepth = 64;
 
 // Global control block of one search, each counter on its own 128-byte line.
 struct Ctl {
-    unsigned head;    unsigned pad0[31];   // queue consumer ticket
-    unsigned tail;    unsigned pad1[31];   // queue producer ticket
-    unsigned pending; unsigned pad2[31];   // frames queued or being expanded
-    unsigned idle;    unsigned pad3[31];   // groups without a frame
-    unsigned abort;   unsigned pad4[31];   // set on error: every warp stops
+    unsigned head;     unsigned pad0[31];  // global queue consumer ticket
+    unsigned tail;     unsigned pad1[31];  // global queue producer ticket
+    unsigned pending;  unsigned pad2[31];  // frames in the global ring + active blocks
+    unsigned starving; unsigned pad3[31];  // blocks with idle groups and no local frame
+    unsigned abort;    unsigned pad4[31];  // set on error: every warp stops
 };
+
+// Per-block frame ring in shared memory (the first level of the work
+// distribution): header, kLocalSlots sequence numbers, kLocalSlots frames.
+constexpr int kLocalSlots = 32;
+struct LocalHdr {
+    unsigned head, tail;  // ring tickets
+    unsigned idle;        // groups of this block without a frame
+    unsigned bwork;       // busy groups + frames in the ring; the block holds
+                          // one unit of Ctl::pending while this is non-zero
+    unsigned starving;    // this block is counted in Ctl::starving
+    unsigned poller;      // a warp of this block is polling the global ring
+    unsigned done;        // the search is over
+    unsigned refreshing;  // a warp is refreshing the cached global state
+    // cached global state (refreshed every few microseconds)
+    unsigned g_head, g_tail, g_starving, g_abort;
+    unsigned long long stamp;
+    unsigned pad[2];
+};
+__host__ __device__ inline size_t frame_words(uint32_t wp) { return (8 + 2 * (size_t)wp + 3) / 4 * 4; }
+__host__ __device__ inline size_t local_queue_bytes(uint32_t wp)
+{
+    return sizeof(LocalHdr) + kLocalSlots * 4 + (size_t)kLocalSlots * frame_words(wp) * 4;
+}
 
 struct SearchParams {
     uint32_t n;             // vertices
@@ -46,7 +69,39 @@ struct SearchParams {
     uint32_t total_groups;
     uint32_t pivot_mode;
     uint32_t stack_levels;  // <= kStackDepth
+    uint32_t split_min_p;   // publish new subtrees with |P| >= this ...
+    uint32_t split_target;  // ... while the global ring holds fewer frames
 };
+
+// One graph of a batch (device table entry; pointers into library memory).
+struct BatchGraph {
+    const uint32_t *rows;   // validated input bitset, w words per row
+    uint32_t *order;        // n entries
+    uint32_t *ren;          // n * wp renumbered words (+ pad to 16 B)
+    uint64_t *out;          // MCE_OUT_WORDS(n) words
+    uint32_t n, w, wp, pad;
+};
+
+struct BatchParams {
+    const BatchGraph *graphs;
+    const uint32_t *list;   // graph indices of this bucket, most expensive first
+    uint32_t count;         // entries of list
+    unsigned *next;         // claim counter (zeroed before the launch)
+    unsigned char *qbase;   // per-block queue regions
+    size_t qstride;         // bytes per region
+    uint32_t qcap, fs;      // slots per region, frame stride (words)
+    uint64_t timeout_ns;
+    uint32_t pivot_mode, stack_levels, groups_per_block;
+    uint32_t split_min_p, split_target;
+};
+
+// Per-block queue region of the batched search: [Ctl | seq | frames]
+__host__ __device__ inline size_t batch_seq_offset() { return 1024; }
+__host__ __device__ inline size_t batch_frames_offset(uint32_t qcap) { return 1024 + (((size_t)qcap * 4 + 255) / 256) * 256; }
+__host__ __device__ inline size_t batch_region_bytes(uint32_t qcap, uint32_t fs)
+{
+    return batch_frames_offset(qcap) + (((size_t)qcap * fs * 4 + 255) / 256) * 256;
+}
 
 struct LaunchShape {
     unsigned blocks, threads;
@@ -60,6 +115,10 @@ struct LaunchShape {
 struct SearchImpl {
     cudaError_t (*run)(const SearchParams &, const LaunchShape &, cudaStream_t);
     cudaError_t (*occupancy)(int threads, size_t smem, int *blocks_per_sm);
+    // batched form: one graph per block at a time (kernel attributes are set
+    // by batch_occupancy, so run_batch is safe inside a stream capture)
+    cudaError_t (*run_batch)(const BatchParams &, const LaunchShape &, cudaStream_t);
+    cudaError_t (*batch_occupancy)(int threads, size_t smem, int *blocks_per_sm);
 };
 SearchImpl search_impl_1_1(bool smem, int pivot);
 SearchImpl search_impl_1_2(bool smem, int pivot);
@@ -86,14 +145,30 @@ cudaError_t launch_order(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t 
 cudaError_t launch_identity(uint32_t n, uint32_t *order, cudaStream_t s);
 cudaError_t launch_renumber(uint32_t n, uint32_t w, const uint32_t *rows, const uint32_t *order,
                             uint32_t wout, uint32_t *rows_out, cudaStream_t s);
+// Batched preprocessing over a device table of graphs (max_n / max_w / max_wp
+// bound every entry).  prepare_* sets kernel attributes (call before capture).
+cudaError_t prepare_order_batch(uint32_t max_n, uint32_t max_w, size_t *smem);
+cudaError_t launch_order_batch(const BatchGraph *graphs, uint32_t count, uint32_t max_n, size_t smem,
+                               cudaStream_t s);
+cudaError_t launch_renumber_batch(const BatchGraph *graphs, uint32_t count, uint32_t max_n, uint32_t max_wp,
+                                  cudaStream_t s);
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Shared-memory layout of the search kernel:
-//   [rows (when staged), padded to 16 B][hv: n x u64][hist: (n + 1) x u32]
+// Shared-memory layout of the search kernels:
+//   [rows (when staged), padded to 16 B][hv: n x u64][hist: (n + 1) x u32,
+//   padded to 16 B][local frame ring]
 __host__ __device__ inline size_t smem_rows_bytes(uint32_t n, uint32_t wp, bool rows_in_smem)
 {
     return rows_in_smem ? ((size_t)n * wp * 4 + 15) / 16 * 16 : 0;
+}
+__host__ __device__ inline size_t smem_local_offset(uint32_t n, uint32_t wp, bool rows_in_smem)
+{
+    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + (((size_t)n + 1) * 4 + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem)
+{
+    return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp);
 }
 
 

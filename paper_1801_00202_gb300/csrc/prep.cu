@@ -3,6 +3,7 @@
 //    list or a bitset,
 //  * the maximum-degree-first ordering (Section 4.2),
 //  * renumbering by position (Section 4.2, "How we use the vertex ordering").
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -67,10 +68,9 @@ __global__ void validate_kernel(uint32_t n, uint32_t w, const uint32_t *__restri
 // with the smallest label.  A round takes the warp maximum, places that
 // vertex and decrements the keys of its remaining neighbours.
 template <int JW>
-__global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
-                                                   uint32_t *__restrict__ order, int rows_in_smem)
+__device__ __forceinline__ void order_body(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
+                                           uint32_t *__restrict__ order, int rows_in_smem, uint32_t *sm)
 {
-    extern __shared__ __align__(16) uint32_t sm[];
     uint32_t *sdeg = sm;                                  // n keys
     uint32_t *srows = sm + ((n + 3u) & ~3u);              // n * w words (optional)
     const uint32_t *R = rows;
@@ -120,6 +120,25 @@ __global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, cons
     }
 }
 
+template <int JW>
+__global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
+                                                   uint32_t *__restrict__ order, int rows_in_smem)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    order_body<JW>(n, w, rows, order, rows_in_smem, sm);
+}
+
+// One block per graph of a batch; the rows go to shared memory when they fit
+// in the launch's dynamic shared memory.
+template <int JW>
+__global__ void __launch_bounds__(256) order_batch_kernel(const BatchGraph *__restrict__ graphs, size_t smem_bytes)
+{
+    extern __shared__ __align__(16) uint32_t sm[];
+    const BatchGraph gd = graphs[blockIdx.x];
+    const size_t need = (size_t)((gd.n + 3u) & ~3u) * 4 + (size_t)gd.n * gd.w * 4;
+    order_body<JW>(gd.n, gd.w, gd.rows, gd.order, need <= smem_bytes, sm);
+}
+
 __global__ void identity_kernel(uint32_t n, uint32_t *order)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) order[i] = i;
@@ -143,6 +162,27 @@ __global__ void renumber_kernel(uint32_t n, uint32_t w, const uint32_t *__restri
         }
         const uint32_t word = __ballot_sync(FULLM, bit);
         if (lane == 0) out[t] = word;
+    }
+}
+
+// Renumbering for a batch: blockIdx.y selects the graph, the block's warps
+// stride over its output words.
+__global__ void renumber_batch_kernel(const BatchGraph *__restrict__ graphs)
+{
+    const BatchGraph gd = graphs[blockIdx.y];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t total = (uint64_t)gd.n * gd.wp;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < total; t += nwarps) {
+        const uint32_t i = (uint32_t)(t / gd.wp), jw = (uint32_t)(t % gd.wp);
+        const uint32_t j = jw * 32u + lane;
+        bool bit = false;
+        if (j < gd.n) {
+            const uint32_t src = gd.order[i], col = gd.order[j];
+            bit = (__ldg(gd.rows + (size_t)src * gd.w + (col >> 5)) >> (col & 31)) & 1u;
+        }
+        const uint32_t word = __ballot_sync(FULLM, bit);
+        if (lane == 0) gd.ren[t] = word;
     }
 }
 
@@ -210,6 +250,41 @@ cudaError_t launch_renumber(uint32_t n, uint32_t w, const uint32_t *rows, const 
     if (n == 0) return cudaSuccess;
     const uint64_t warps = (uint64_t)n * wout;
     renumber_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(n, w, rows, order, wout, rows_out);
+    return cudaGetLastError();
+}
+
+
+cudaError_t prepare_order_batch(uint32_t max_n, uint32_t max_w, size_t *smem)
+{
+    const size_t keys = ((max_n + 3u) & ~3u) * sizeof(uint32_t);
+    const size_t rbytes = (size_t)max_n * max_w * 4;
+    *smem = keys + ((keys + rbytes) <= 200u * 1024u ? rbytes : 0);
+    const uint32_t words = (max_n + 31) / 32;
+    cudaError_t e;
+    if (words <= 32) e = cudaFuncSetAttribute(order_batch_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    else if (words <= 64) e = cudaFuncSetAttribute(order_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    else e = cudaFuncSetAttribute(order_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    return e;
+}
+
+cudaError_t launch_order_batch(const BatchGraph *graphs, uint32_t count, uint32_t max_n, size_t smem, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const uint32_t words = (max_n + 31) / 32;
+    if (words <= 32) order_batch_kernel<1><<<count, 256, smem, s>>>(graphs, smem);
+    else if (words <= 64) order_batch_kernel<2><<<count, 256, smem, s>>>(graphs, smem);
+    else order_batch_kernel<4><<<count, 256, smem, s>>>(graphs, smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_renumber_batch(const BatchGraph *graphs, uint32_t count, uint32_t max_n, uint32_t max_wp,
+                                  cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const uint64_t warps = (uint64_t)max_n * max_wp;
+    unsigned gx = (unsigned)std::min<uint64_t>((warps + 7) / 8, 1024);
+    if (gx == 0) gx = 1;
+    renumber_batch_kernel<<<dim3(gx, count), 256, 0, s>>>(graphs);
     return cudaGetLastError();
 }
 

@@ -17,13 +17,16 @@
 //    local memory (no recursion).  A frame is pushed only while it has
 //    children left, so single-child chains (e.g. a complete graph) do not
 //    grow the stack.
-//  * Idle groups take frames from a global bounded MPMC queue; busy groups
-//    give away the upper half of their shallowest frame's branching set when
-//    idle groups outnumber queued frames.  Splitting a branching set L into
-//    a lower part L1 (kept) and upper part L2 (given away) as
-//    (P, X, end = min L2) and (P \ L1, X u L1, end) reproduces exactly the
-//    sequential P/X updates of Alg. 4, so node counts do not depend on how
-//    the work was split.
+//  * Work moves at two levels.  Idle groups take frames from their block's
+//    ring in shared memory, which busy groups of the block refill by giving
+//    away the front half of their shallowest branching set; blocks whose
+//    groups are idle with an empty ring count as starving, one idle warp per
+//    block polls the global ring (a bounded MPMC ring in global memory), and
+//    busy groups feed that ring while starving blocks outnumber its frames.
+//    Cutting a branching set L into a front part L1 (given) and the rest as
+//    (P, X, end = first kept element) and (P \ L1, X u L1, end) reproduces
+//    exactly the sequential P/X updates of Alg. 4, so node counts do not
+//    depend on how the work was split.
 //  * Leaves update per-group register counters; sizes go to a shared-memory
 //    histogram; everything is integer arithmetic modulo 2^64, so the
 //    reduction order does not matter and results are bit-exact.
@@ -40,8 +43,44 @@
 namespace mce {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr unsigned kCheckEvery = 8;      // iterations between queue polls
+constexpr unsigned kLocalCheck = 4;      // busy warps: iterations between local-ring checks
+constexpr unsigned kGlobalCheck = 16;    // busy warps: iterations between global checks
 constexpr unsigned kCasTries = 1u << 14; // bound of one queue ticket loop
+// Smallest candidate set |P| of a frame worth giving away, per level: a
+// frame is a whole subtree, so tiny ones cost more to move than to expand.
+constexpr int kMinShareLocal = 20;
+constexpr int kMinShareGlobal = 28;
+constexpr uint64_t kRefreshNs = 2000;    // age of the cached global state
+
+// Default split threshold by edge density p = i/40 (i = 1..39): the smallest
+// candidate-set size k whose random subgraph G(k, p) has at least 64 maximal
+// cliques in expectation (sum_j C(k,j) p^C(j,2) (1-p^j)^(k-j) >= 64), so a
+// published subtree carries enough work to pay for the move.
+__constant__ unsigned char kSplitByDensity[39] = {66, 52, 45, 41, 38, 36, 34, 33, 31, 30, 29, 28, 27,
+                                                  26, 25, 24, 24, 23, 23, 22, 21, 21, 21, 20, 20, 20,
+                                                  19, 19, 19, 19, 19, 19, 19, 19, 19, 20, 21, 23, 28};
+
+// Split threshold for a block's graph: the caller's value, else the table
+// entry for the density of the staged rows.  Whole block; returns the same
+// value in every thread.
+__device__ __forceinline__ unsigned split_threshold(const uint32_t *rows, uint32_t n, uint32_t wp, uint32_t fixed,
+                                                    unsigned *scratch_u32)
+{
+    if (fixed) return fixed;
+    if (threadIdx.x == 0) *scratch_u32 = 0u;
+    __syncthreads();
+    unsigned mine = 0;
+    for (uint32_t i = threadIdx.x; i < n * wp; i += blockDim.x) mine += __popc(rows[i]);
+    atomicAdd(scratch_u32, mine);
+    __syncthreads();
+    const unsigned deg_sum = *scratch_u32;
+    __syncthreads();
+    if (n < 2) return 0xffffffffu;
+    const double pd = (double)deg_sum / ((double)n * (double)(n - 1));
+    int i = (int)(pd * 40.0 + 0.5);
+    i = i < 1 ? 1 : (i > 39 ? 39 : i);
+    return kSplitByDensity[i - 1];
+}
 
 // SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014), the mixing step
 // of the clique hash h(K) = mix64(S(K) ^ mix64(|K|)).
@@ -238,34 +277,122 @@ __device__ __forceinline__ void load_row(uint32_t (&r)[K], const uint32_t *p)
 }
 
 // ---------------------------------------------------------------------------
-// Give away the upper part of a frame's branching set L (c elements).  The
-// owner keeps the lowest `keep` of them:
-//   kKeepHalf       keep = ceil(c/2); a single element is not given away;
-//   kKeepHalfOrNone keep = ceil(c/2) for c >= 2, else 0 (the whole frame);
-//   kKeepNone       keep = 0.
-// The given-away frame is (P \ L1, X u L1, pivot, end) with L1 the kept part;
-// the owner continues with end = the first given-away position, which the
-// call returns (or -1 when nothing was given).  `whole` tells the owner that
-// it kept nothing.
-enum KeepPolicy { kKeepHalf = 0, kKeepHalfOrNone = 1, kKeepNone = 2 };
+// Block-local frame ring (shared memory): the same per-slot sequence-number
+// protocol as the global ring, with block-scope atomics.
 
-template <int G, int K>
-__device__ __forceinline__ int donate(const Grp<G, K> &g, const SearchParams &prm, bool pred, int policy,
-                                      const uint32_t (&P)[K], const uint32_t (&X)[K], const uint32_t (&L)[K],
-                                      unsigned pe, unsigned rs, uint64_t S, bool &whole, uint64_t &c_don)
+__device__ __forceinline__ unsigned vld(const unsigned *p) { return *reinterpret_cast<const volatile unsigned *>(p); }
+__device__ __forceinline__ void vst(unsigned *p, unsigned v) { *reinterpret_cast<volatile unsigned *>(p) = v; }
+
+__device__ __forceinline__ bool lq_reserve_push(LocalHdr *h, unsigned *seq, unsigned &ticket)
+{
+    unsigned pos = vld(&h->tail);
+    for (unsigned t = 0; t < 256; ++t) {
+        const unsigned s = vld(&seq[pos & (kLocalSlots - 1)]);
+        const int dif = (int)(s - pos);
+        if (dif == 0) {
+            const unsigned prev = atomicCAS(&h->tail, pos, pos + 1);
+            if (prev == pos) { ticket = pos; return true; }
+            pos = prev;
+        } else if (dif < 0) {
+            return false;
+        } else {
+            pos = vld(&h->tail);
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool lq_reserve_pop(LocalHdr *h, unsigned *seq, unsigned &ticket)
+{
+    unsigned pos = vld(&h->head);
+    for (unsigned t = 0; t < 256; ++t) {
+        const unsigned s = vld(&seq[pos & (kLocalSlots - 1)]);
+        const int dif = (int)(s - (pos + 1));
+        if (dif == 0) {
+            const unsigned prev = atomicCAS(&h->head, pos, pos + 1);
+            if (prev == pos) { ticket = pos; return true; }
+            pos = prev;
+        } else if (dif < 0) {
+            return false;
+        } else {
+            pos = vld(&h->head);
+        }
+    }
+    return false;
+}
+
+struct LocalQ {
+    LocalHdr *h;
+    unsigned *seq;
+    uint32_t *frames;
+};
+
+__device__ __forceinline__ LocalQ local_queue_at(unsigned char *base, uint32_t wp)
+{
+    LocalQ q;
+    q.h = reinterpret_cast<LocalHdr *>(base);
+    q.seq = reinterpret_cast<unsigned *>(base + sizeof(LocalHdr));
+    q.frames = reinterpret_cast<uint32_t *>(base + sizeof(LocalHdr) + kLocalSlots * 4);
+    (void)wp;
+    return q;
+}
+
+// Reset the block's ring (whole block; a barrier must follow).
+__device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned groups)
+{
+    for (unsigned i = threadIdx.x; i < (unsigned)kLocalSlots; i += blockDim.x) q.seq[i] = i;
+    if (threadIdx.x == 0) {
+        q.h->head = 0u;
+        q.h->tail = 0u;
+        q.h->idle = groups;
+        q.h->bwork = 0u;
+        q.h->starving = 0u;
+        q.h->poller = 0u;
+        q.h->done = 0u;
+        q.h->refreshing = 0u;
+        q.h->g_head = 0u;
+        q.h->g_tail = 0u;
+        q.h->g_starving = 0u;
+        q.h->g_abort = 0u;
+        q.h->stamp = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Give away the front of a frame's branching set L (c elements, in order).
+// The taker gets L1 = the first `give` elements as the frame
+// (P, X, pivot, end = first kept element); the giver keeps the rest as
+// (P \ L1, X u L1, pivot, end).  Walking L1 then the rest is exactly the
+// sequential loop of Alg. 4 (each child sees P minus, and X plus, every
+// earlier sibling), so the search tree is the same however often it is cut.
+// give = floor(c/2) for c >= 2; with c == 1 the whole frame goes only when
+// `allow_whole`.  A frame whose candidate set has fewer than `min_p` vertices
+// is kept.  Returns true when a frame was handed over; the giver then applies
+// (P, X, L) &= ~L1 / |= L1 through the returned mask l1 (its own words).
+
+template <int G, int K, bool LOCAL>
+__device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchParams &prm, const LocalQ &lq,
+                                             bool pred, bool allow_whole, int min_p, const uint32_t (&P)[K],
+                                             const uint32_t (&X)[K], const uint32_t (&L)[K], unsigned pe,
+                                             unsigned rs, uint64_t S, uint32_t (&l1)[K], bool &whole, uint64_t &c_don)
 {
     constexpr int WP = G * K;
-    int cl = 0;
+    int cl = 0, cp = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) cl += __popc(L[k]);
+    for (int k = 0; k < K; ++k) {
+        cl += __popc(L[k]);
+        cp += __popc(P[k]);
+    }
     const int c = g.sum(cl);
-    int keep = 0;
-    if (policy != kKeepNone) keep = (c >= 2) ? (c + 1) / 2 : (policy == kKeepHalf ? c : 0);
-    const bool ok = pred && c > keep;
+    const int np = g.sum(cp);
+    const int give = (c >= 2) ? c / 2 : ((c == 1 && allow_whole) ? 1 : 0);
+    const bool ok = pred && give > 0 && np >= min_p;
+    // split = position of element #give of L (the first one kept), or the
+    // frame's end when everything goes
     const int pre = g.excl_scan(cl);
     int pos = -1;
-    if (ok && pre <= keep && keep < pre + cl) {
-        int r = keep - pre;
+    if (ok && give < c && pre <= give && give < pre + cl) {
+        int r = give - pre;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int cw = __popc(L[k]);
@@ -282,25 +409,189 @@ __device__ __forceinline__ int donate(const Grp<G, K> &g, const SearchParams &pr
     }
     int split = pos;
     if (G > 1) {
-        unsigned b = __ballot_sync(FULL, pos >= 0) & g.gmask;
+        const unsigned b = __ballot_sync(FULL, pos >= 0) & g.gmask;
         split = __shfl_sync(FULL, pos, b ? (__ffs(b) - 1) : (int)g.lane);
     }
+    if (give >= c) split = (int)(pe >> 16);
 
+    // A frame in the block ring is block work (the giver keeps the block
+    // active); a frame in the global ring is one unit of global pending.
     unsigned ticket = 0, got = 0;
     if (ok && g.leader()) {
+        if (LOCAL) {
+            atomicAdd(&lq.h->bwork, 1u);
+            got = lq_reserve_push(lq.h, lq.seq, ticket) ? 1u : 0u;
+            if (!got) atomicSub(&lq.h->bwork, 1u);
+        } else {
+            atomicAdd(&prm.ctl->pending, 1u);
+            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket) ? 1u : 0u;
+            if (!got) atomicSub(&prm.ctl->pending, 1u);
+        }
+    }
+    got = g.from_leader(got);
+    ticket = g.from_leader(ticket);
+    const unsigned npe = (pe & 0xffffu) | ((unsigned)split << 16);
+#pragma unroll
+    for (int k = 0; k < K; ++k) l1[k] = got ? (L[k] & g.below(k, (unsigned)split)) : 0u;
+    if (got) {
+        if (LOCAL) {
+            volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * frame_words(WP);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                fr[kFrameHdr + g.gl * K + k] = P[k];
+                fr[kFrameHdr + WP + g.gl * K + k] = X[k];
+            }
+            if (g.leader()) {
+                fr[0] = npe;
+                fr[1] = rs;
+                fr[2] = (uint32_t)S;
+                fr[3] = (uint32_t)(S >> 32);
+            }
+            __threadfence_block();
+        } else {
+            uint32_t *fr = prm.frames + (size_t)(ticket & (prm.qcap - 1u)) * prm.fs;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                __stcg(fr + kFrameHdr + g.gl * K + k, P[k]);
+                __stcg(fr + kFrameHdr + WP + g.gl * K + k, X[k]);
+            }
+            if (g.leader()) {
+                __stcg(fr + 0, npe);
+                __stcg(fr + 1, rs);
+                __stcg(fr + 2, (uint32_t)S);
+                __stcg(fr + 3, (uint32_t)(S >> 32));
+            }
+            __threadfence();
+        }
+    }
+    __syncwarp();
+    if (got && g.leader()) {
+        if (LOCAL) {
+            __threadfence_block();
+            vst(&lq.seq[ticket & (kLocalSlots - 1)], ticket + 1u);
+        } else {
+            st_release(&prm.seq[ticket & (prm.qcap - 1u)], ticket + 1u);
+        }
+        ++c_don;
+    }
+    whole = give >= c;
+    return got != 0u;
+}
+
+// Per-warp result counters (meaningful in group leaders; summed at the end).
+struct Counters {
+    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0;
+    unsigned max = 0;
+};
+
+// Warp-reduce the counters and add them to out[] (one atomic per counter per
+// warp).  Called by all 32 lanes.
+__device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c.cnt += __shfl_xor_sync(FULL, c.cnt, o);
+        c.nodes += __shfl_xor_sync(FULL, c.nodes, o);
+        c.intl += __shfl_xor_sync(FULL, c.intl, o);
+        c.dead += __shfl_xor_sync(FULL, c.dead, o);
+        c.hash += __shfl_xor_sync(FULL, c.hash, o);
+        c.don += __shfl_xor_sync(FULL, c.don, o);
+        c.steals += __shfl_xor_sync(FULL, c.steals, o);
+        c.max = max(c.max, __shfl_xor_sync(FULL, c.max, o));
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
+        if (c.cnt) atomicAdd(o + MCE_OUT_COUNT, c.cnt);
+        if (c.nodes) atomicAdd(o + MCE_OUT_NODES, c.nodes);
+        if (c.intl) atomicAdd(o + MCE_OUT_INTERNAL, c.intl);
+        if (c.dead) atomicAdd(o + MCE_OUT_DEAD_ENDS, c.dead);
+        if (c.hash) atomicAdd(o + MCE_OUT_HASH, c.hash);
+        if (c.don) atomicAdd(o + MCE_OUT_DONATIONS, c.don);
+        if (c.steals) atomicAdd(o + MCE_OUT_STEALS, c.steals);
+        if (c.max) atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)c.max);
+    }
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the barrier at mb: ~2 s, then false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    for (unsigned t = 0;; ++t) {
+        if (mbar_try_wait(mb, parity)) return true;
+        if ((t & 63u) == 63u && global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+// Stage `bytes` (multiple of 16, 16-byte aligned ends) of rows from global to
+// shared memory with 1-D bulk copies completing on the barrier at mb.  Thread 0
+// issues; every thread waits (bounded) for phase `parity`.  Returns false on a
+// timeout, after a second bounded wait that lets copies in flight land before
+// the shared memory can be reused.  Must be called by the whole block.
+__device__ __forceinline__ bool stage_rows(uint32_t *sdst, const uint32_t *gsrc, uint32_t bytes, uint32_t mb,
+                                           uint32_t parity)
+{
+    if (threadIdx.x == 0) {
+        // order earlier generic-proxy reads of this shared memory before the
+        // async-proxy writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+        const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(sdst);
+        for (uint32_t off = 0; off < bytes; off += 65536u) {
+            const uint32_t len = (bytes - off) < 65536u ? (bytes - off) : 65536u;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst0 + off),
+                "l"(reinterpret_cast<const unsigned char *>(gsrc) + off), "r"(len), "r"(mb)
+                : "memory");
+        }
+    }
+    if (mbar_wait_bounded(mb, parity)) return true;
+    mbar_wait_bounded(mb, parity);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Publish a frame (P, X, pivot|end, |R|, S) as it stands to the global ring
+// (one unit of global pending).  Warp-uniform call; true where it went.
+template <int G, int K>
+__device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchParams &prm, bool pred,
+                                            const uint32_t (&P)[K], const uint32_t (&X)[K], unsigned pe, unsigned rs,
+                                            uint64_t S)
+{
+    constexpr int WP = G * K;
+    const unsigned qmask = prm.qcap - 1u;
+    unsigned ticket = 0, got = 0;
+    if (pred && g.leader()) {
         atomicAdd(&prm.ctl->pending, 1u);
-        got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket) ? 1u : 0u;
+        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket) ? 1u : 0u;
         if (!got) atomicSub(&prm.ctl->pending, 1u);
     }
     got = g.from_leader(got);
     ticket = g.from_leader(ticket);
     if (got) {
-        uint32_t *fr = prm.frames + (size_t)(ticket & (prm.qcap - 1u)) * prm.fs;
+        uint32_t *fr = prm.frames + (size_t)(ticket & qmask) * prm.fs;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const uint32_t l1 = L[k] & g.below(k, (unsigned)split);
-            __stcg(fr + kFrameHdr + g.gl * K + k, P[k] & ~l1);
-            __stcg(fr + kFrameHdr + WP + g.gl * K + k, X[k] | l1);
+            __stcg(fr + kFrameHdr + g.gl * K + k, P[k]);
+            __stcg(fr + kFrameHdr + WP + g.gl * K + k, X[k]);
         }
         if (g.leader()) {
             __stcg(fr + 0, pe);
@@ -311,94 +602,27 @@ __device__ __forceinline__ int donate(const Grp<G, K> &g, const SearchParams &pr
         __threadfence();
     }
     __syncwarp();
-    if (got && g.leader()) {
-        st_release(&prm.seq[ticket & (prm.qcap - 1u)], ticket + 1u);
-        ++c_don;
-    }
-    whole = (keep == 0);
-    return got ? split : -1;
+    if (got && g.leader()) st_release(&prm.seq[ticket & qmask], ticket + 1u);
+    return got != 0u;
 }
 
-// ---------------------------------------------------------------------------
-
+// The search proper: the groups of this warp expand frames until the search
+// is over or aborts.  Work moves at two levels: idle groups take frames from
+// the block's shared-memory ring, which busy groups of the block refill by
+// giving away the front of their shallowest branching set; a block with idle
+// groups and an empty ring counts itself as starving, one of its idle warps
+// polls the global ring, and busy groups feed the global ring while starving
+// blocks outnumber its frames.  rows, hv, hist, lq are this block's staged
+// rows (or global rows), vertex hash terms, clique-size histogram and ring.
+// Called by all 32 lanes of every warp.
 template <int G, int K, bool SMEM, int PIVOT>
-__global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const SearchParams prm)
+__device__ __forceinline__ void search_loop(const SearchParams &prm, const uint32_t *rows, const uint64_t *hv,
+                                            uint32_t *hist, const LocalQ &lq, unsigned split_min, Counters &cn)
 {
     using Gp = Grp<G, K>;
     constexpr int WP = G * K;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ int stage_failed;
-
     const uint32_t n = prm.n;
-    const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
-    uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
-    uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
     Ctl *ctl = prm.ctl;
-
-    // ---- prologue: stage the rows (bulk copy), hash table, histogram
-    if (threadIdx.x == 0) stage_failed = 0;
-    if (SMEM) {
-        const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"((uint32_t)rbytes)
-                         : "memory");
-            const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(srows);
-            for (size_t off = 0; off < rbytes; off += 65536) {
-                const uint32_t len = (uint32_t)((rbytes - off) < 65536 ? (rbytes - off) : 65536);
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        dst0 + (uint32_t)off),
-                    "l"(reinterpret_cast<const unsigned char *>(prm.rows) + off), "r"(len), "r"(mb)
-                    : "memory");
-            }
-        }
-    }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) hv[i] = mix64((uint64_t)prm.order[i] + 1u);
-    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hist[i] = 0u;
-    if (SMEM) {
-        // bounded wait for the bulk copy (phase 0)
-        const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
-        bool done = false;
-        const uint64_t t0 = global_ns();
-        for (unsigned t = 0; !done; ++t) {
-            uint32_t ok;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(ok)
-                : "r"(mb)
-                : "memory");
-            done = ok != 0;
-            if (!done && (t & 63u) == 63u && global_ns() - t0 > 2000000000ull) break;
-        }
-        if (!done) {
-            stage_failed = 1;
-            if (threadIdx.x == 0) set_status(prm.out, ctl, MCE_ETIMEOUT);
-            // give copies still in flight a second bounded chance to land
-            // before the block retires its shared memory
-            const uint64_t t1 = global_ns();
-            for (unsigned t = 0; !done; ++t) {
-                uint32_t ok;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                    : "=r"(ok)
-                    : "r"(mb)
-                    : "memory");
-                done = ok != 0;
-                if (!done && (t & 63u) == 63u && global_ns() - t1 > 2000000000ull) break;
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t *rows = SMEM ? srows : prm.rows;
-
     Gp g;
     g.init();
     uint32_t P[K], X[K], L[K];
@@ -408,8 +632,8 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
     uint64_t S = 0;
     int d = 0, dbase = 0;
     bool work = false;
-    uint64_t c_cnt = 0, c_nodes = 0, c_int = 0, c_dead = 0, c_hash = 0, c_don = 0;
-    unsigned c_max = 0;
+    bool poller = false;
+    unsigned gq = 0;  // global ring length last seen
 
     uint32_t stP[kStackDepth][K], stX[kStackDepth][K];
     unsigned stPE[kStackDepth], stRS[kStackDepth];
@@ -418,13 +642,82 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
     uint64_t quiet_since = 0;
     const uint64_t t_start = global_ns();
     unsigned last_pend = 0xffffffffu, last_head = 0xffffffffu;
-    unsigned backoff = 64;
+    unsigned backoff = 32;
     const unsigned qmask = prm.qcap - 1u;
-    bool stop = stage_failed != 0;
+    const size_t lfs = frame_words(WP);
 
     auto rowp = [&](int v) -> const uint32_t * { return rows + (size_t)v * WP + g.gl * K; };
 
-    for (unsigned it = 0; !stop; ++it) {
+    // Take (P, X, pivot|end, |R|, S) as this group's frame.
+    auto start_frame = [&]() {
+        work = true;
+        d = dbase = 0;
+        uint32_t rp[K];
+        load_row<K, SMEM>(rp, rowp((int)(pe & 0xffffu)));
+#pragma unroll
+        for (int k = 0; k < K; ++k) L[k] = P[k] & ~rp[k] & g.below(k, pe >> 16);
+    };
+
+    // Share the shallowest frame this group owns (the stack bottom, else the
+    // current frame) through level LOCAL (true: block ring, false: global).
+    auto share = [&](bool want, bool local) {
+        const bool from_stack = want && d > dbase;
+        uint32_t sP[K], sX[K], sL[K], l1[K];
+        unsigned spe = pe, srs = rs;
+        uint64_t sS = S;
+        if (from_stack) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                sP[k] = stP[dbase][k];
+                sX[k] = stX[dbase][k];
+            }
+            spe = stPE[dbase];
+            if (g.leader()) {
+                srs = stRS[dbase];
+                sS = stS[dbase];
+            }
+            uint32_t rp[K];
+            load_row<K, SMEM>(rp, rowp((int)(spe & 0xffffu)));
+#pragma unroll
+            for (int k = 0; k < K; ++k) sL[k] = sP[k] & ~rp[k] & g.below(k, spe >> 16);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                sP[k] = P[k];
+                sX[k] = X[k];
+                sL[k] = L[k];
+            }
+        }
+        bool whole = false, gave;
+        if (local)
+            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, kMinShareLocal, sP, sX, sL, spe, srs, sS, l1,
+                                            whole, cn.don);
+        else
+            gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, kMinShareGlobal, sP, sX, sL, spe, srs, sS,
+                                             l1, whole, cn.don);
+        if (gave) {
+            if (from_stack) {
+                if (whole) {
+                    ++dbase;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        stP[dbase][k] = sP[k] & ~l1[k];
+                        stX[dbase][k] = sX[k] | l1[k];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    P[k] &= ~l1[k];
+                    X[k] |= l1[k];
+                    L[k] &= ~l1[k];
+                }
+            }
+        }
+    };
+
+    for (unsigned it = 0;; ++it) {
         // ---- A: a frame whose branching set is exhausted returns to its parent
         const bool hasL = g.any(L);
         if (work && !hasL) {
@@ -447,37 +740,124 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
             } else {
                 work = false;
                 if (g.leader()) {
-                    atomicSub(&ctl->pending, 1u);
-                    atomicAdd(&ctl->idle, 1u);
+                    atomicAdd(&lq.h->idle, 1u);
+                    // the last work of the block gives back its unit
+                    if (atomicSub(&lq.h->bwork, 1u) == 1u) atomicSub(&ctl->pending, 1u);
                 }
             }
         }
 
-        // ---- B: queue traffic (every kCheckEvery iterations, or when idle)
-        const bool all_idle = __ballot_sync(FULL, work) == 0u;
-        if (all_idle || (it % kCheckEvery) == 0u) {
-            unsigned head = 0, tail = 0, idl = 0, pend = 0, ab = 0;
+        // ---- B1: the block ring (idle groups take, busy groups refill)
+        const unsigned busy_b = __ballot_sync(FULL, work);
+        if (busy_b != FULL || (it % kLocalCheck) == 0u) {
+            unsigned lh = 0, lt = 0, li = 0, ld = 0;
             if (g.lane == 0) {
-                ab = ld_relaxed(&ctl->abort);
-                pend = ld_relaxed(&ctl->pending);
-                head = ld_relaxed(&ctl->head);
-                tail = ld_relaxed(&ctl->tail);
-                idl = ld_relaxed(&ctl->idle);
+                lh = vld(&lq.h->head);
+                lt = vld(&lq.h->tail);
+                li = vld(&lq.h->idle);
+                ld = vld(&lq.h->done);
             }
+            lh = __shfl_sync(FULL, lh, 0);
+            lt = __shfl_sync(FULL, lt, 0);
+            li = __shfl_sync(FULL, li, 0);
+            ld = __shfl_sync(FULL, ld, 0);
+            if (busy_b == 0u && ld) break;
+            const unsigned lqueued = lt - lh;
+            unsigned ticket = 0, got = 0;
+            if (!work && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, ticket) ? 1u : 0u;
+            got = g.from_leader(got);
+            ticket = g.from_leader(ticket);
+            if (got) {
+                __threadfence_block();
+                const volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * lfs;
+                pe = fr[0];
+                rs = fr[1];
+                S = (uint64_t)fr[2] | ((uint64_t)fr[3] << 32);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    P[k] = fr[kFrameHdr + g.gl * K + k];
+                    X[k] = fr[kFrameHdr + WP + g.gl * K + k];
+                }
+            }
+            __syncwarp();
+            if (got) {
+                if (g.leader()) {
+                    __threadfence_block();
+                    vst(&lq.seq[ticket & (kLocalSlots - 1)], ticket + kLocalSlots);
+                    atomicSub(&lq.h->idle, 1u);
+                    ++cn.steals;
+                }
+                start_frame();
+            }
+            const bool hungry = work && !got && li > lqueued;
+            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, true);
+        }
+
+        // ---- B2: the global ring and the end of the search.  Global state is
+        // read by the block's polling warp (an all-idle warp) or, at most
+        // every kRefreshNs, by one busy warp, and cached in shared memory.
+        const unsigned busy2 = __ballot_sync(FULL, work);
+        if (busy2 == 0u || (it % kGlobalCheck) == 0u) {
+            unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
+            bool pol = poller;
+            if (g.lane == 0) {
+                lh = vld(&lq.h->head);
+                lt = vld(&lq.h->tail);
+                if (busy2 == 0u && !pol) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
+                const uint64_t now = global_ns();
+                bool refresh = pol;
+                if (!refresh && now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) > kRefreshNs)
+                    refresh = atomicCAS(&lq.h->refreshing, 0u, 1u) == 0u;
+                if (refresh) {
+                    ab = ld_relaxed(&ctl->abort);
+                    pend = ld_relaxed(&ctl->pending);
+                    head = ld_relaxed(&ctl->head);
+                    tail = ld_relaxed(&ctl->tail);
+                    starving = ld_relaxed(&ctl->starving);
+                    // this block is starving while it has idle groups and an empty ring
+                    const bool st = vld(&lq.h->idle) != 0u && lt == lh;
+                    if (st != (vld(&lq.h->starving) != 0u)) {
+                        if (st) {
+                            if (atomicExch(&lq.h->starving, 1u) == 0u) atomicAdd(&ctl->starving, 1u);
+                        } else {
+                            if (atomicExch(&lq.h->starving, 0u) == 1u) atomicSub(&ctl->starving, 1u);
+                        }
+                    }
+                    vst(&lq.h->g_head, head);
+                    vst(&lq.h->g_tail, tail);
+                    vst(&lq.h->g_starving, starving);
+                    vst(&lq.h->g_abort, ab);
+                    if (ab || pend == 0u) vst(&lq.h->done, 1u);
+                    *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) = now;
+                    if (now - t_start > 10ull * prm.timeout_ns) set_status(prm.out, ctl, MCE_ETIMEOUT);
+                    if (!pol) atomicExch(&lq.h->refreshing, 0u);
+                } else {
+                    head = vld(&lq.h->g_head);
+                    tail = vld(&lq.h->g_tail);
+                    starving = vld(&lq.h->g_starving);
+                    ab = vld(&lq.h->g_abort);
+                }
+                done = vld(&lq.h->done);
+            }
+            pol = __shfl_sync(FULL, pol ? 1u : 0u, 0) != 0u;
+            poller = pol;
             ab = __shfl_sync(FULL, ab, 0);
             pend = __shfl_sync(FULL, pend, 0);
             head = __shfl_sync(FULL, head, 0);
             tail = __shfl_sync(FULL, tail, 0);
-            idl = __shfl_sync(FULL, idl, 0);
+            starving = __shfl_sync(FULL, starving, 0);
+            lh = __shfl_sync(FULL, lh, 0);
+            lt = __shfl_sync(FULL, lt, 0);
+            done = __shfl_sync(FULL, done, 0);
             if (ab) break;
-            if (all_idle && pend == 0u) break;
-            // hard cap on the whole search: ten idle budgets
-            if (g.lane == 0 && global_ns() - t_start > 10ull * prm.timeout_ns) set_status(prm.out, ctl, MCE_ETIMEOUT);
+            if (busy2 == 0u && done) break;
             const unsigned queued = tail - head;
+            gq = queued;
 
-            // idle groups take a frame
+            // idle groups take a global frame when their block's ring is empty
             unsigned ticket = 0, got = 0;
-            if (!work && queued != 0u && g.leader()) got = q_reserve_pop(ctl, prm.seq, qmask, ticket) ? 1u : 0u;
+            if (!work && queued != 0u && lt == lh && g.leader())
+                got = q_reserve_pop(ctl, prm.seq, qmask, ticket) ? 1u : 0u;
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
             if (got) {
@@ -496,65 +876,27 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
             if (got) {
                 if (g.leader()) {
                     st_release(&prm.seq[ticket & qmask], ticket + prm.qcap);
-                    atomicSub(&ctl->idle, 1u);
+                    atomicSub(&lq.h->idle, 1u);
+                    // an already active block absorbs the frame's unit
+                    if (atomicAdd(&lq.h->bwork, 1u) != 0u) atomicSub(&ctl->pending, 1u);
+                    ++cn.steals;
                 }
-                work = true;
-                d = dbase = 0;
-                uint32_t rp[K];
-                load_row<K, SMEM>(rp, rowp((int)(pe & 0xffffu)));
-#pragma unroll
-                for (int k = 0; k < K; ++k) L[k] = P[k] & ~rp[k] & g.below(k, pe >> 16);
+                start_frame();
+            }
+            if (poller && __ballot_sync(FULL, work) != 0u) {
+                // busy now: hand the polling role to another idle warp
+                if (g.lane == 0) atomicExch(&lq.h->poller, 0u);
+                poller = false;
             }
 
-            // busy groups feed idle ones: split the shallowest frame
-            const bool hungry = work && !got && idl > queued;
-            if (__ballot_sync(FULL, hungry) != 0u) {
-                const bool from_stack = hungry && d > dbase;
-                uint32_t sP[K], sX[K], sL[K];
-                unsigned spe = pe, srs = rs;
-                uint64_t sS = S;
-                if (from_stack) {
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        sP[k] = stP[dbase][k];
-                        sX[k] = stX[dbase][k];
-                    }
-                    spe = stPE[dbase];
-                    if (g.leader()) {
-                        srs = stRS[dbase];
-                        sS = stS[dbase];
-                    }
-                    uint32_t rp[K];
-                    load_row<K, SMEM>(rp, rowp((int)(spe & 0xffffu)));
-#pragma unroll
-                    for (int k = 0; k < K; ++k) sL[k] = sP[k] & ~rp[k] & g.below(k, spe >> 16);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        sP[k] = P[k];
-                        sX[k] = X[k];
-                        sL[k] = L[k];
-                    }
-                }
-                bool whole = false;
-                const int ne = donate<G, K>(g, prm, hungry, from_stack ? kKeepHalfOrNone : kKeepHalf, sP, sX, sL, spe,
-                                            srs, sS, whole, c_don);
-                if (ne >= 0) {
-                    const unsigned npe = (spe & 0xffffu) | ((unsigned)ne << 16);
-                    if (from_stack) {
-                        if (whole) ++dbase;
-                        else stPE[dbase] = npe;
-                    } else {
-                        pe = npe;
-#pragma unroll
-                        for (int k = 0; k < K; ++k) L[k] &= g.below(k, (unsigned)ne);
-                    }
-                }
-            }
+            // busy groups feed starving blocks
+            const bool hungry = work && !got && starving > queued;
+            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, false);
 
             if (__ballot_sync(FULL, work) == 0u) {
-                // nobody here has work: back off, watch for a stalled search
-                if (g.lane == 0) {
+                // nobody here has work: back off; the poller watches for a
+                // stalled search
+                if (g.lane == 0 && poller) {
                     const uint64_t now = global_ns();
                     if (pend != last_pend || head != last_head || quiet_since == 0) {
                         quiet_since = now;
@@ -565,10 +907,10 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
                     }
                 }
                 __nanosleep(backoff);
-                backoff = backoff < 2048u ? backoff * 2u : 2048u;
+                backoff = backoff < 1024u ? backoff * 2u : 1024u;
                 continue;
             }
-            backoff = 64;
+            backoff = 32;
         }
 
         // ---- C: expand one child v = first(L) of every active frame
@@ -594,22 +936,22 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
         const bool bx = g.any(Xc);
         uint64_t Sc = 0;
         if (act && g.leader()) {
-            ++c_nodes;
+            ++cn.nodes;
             Sc = S + hv[v];
             if (!bp) {
                 if (!bx) {  // P u X empty: R u {v} is a maximal clique
                     const unsigned k = rs + 1u;
-                    ++c_cnt;
-                    c_hash += mix64(Sc ^ mix64((uint64_t)k));
-                    c_max = k > c_max ? k : c_max;
+                    ++cn.cnt;
+                    cn.hash += mix64(Sc ^ mix64((uint64_t)k));
+                    cn.max = k > cn.max ? k : cn.max;
                     const unsigned old = atomicAdd(&hist[k], 1u);
                     if (old == 0xffffffffu)
                         atomicAdd(reinterpret_cast<unsigned long long *>(prm.out + MCE_OUT_HIST + k), 1ull << 32);
                 } else {
-                    ++c_dead;
+                    ++cn.dead;
                 }
             } else {
-                ++c_int;
+                ++cn.intl;
             }
         }
         const bool inter = act && bp;
@@ -669,7 +1011,24 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
         }
         const bool hasLc = g.any(Lc);
         const bool more = g.any(L);
-        const bool desc = inter && hasLc;
+        bool desc = inter && hasLc;
+        // Breadth-first split of the top of the tree: a new subtree with a
+        // large candidate set goes to the global ring (while the ring is short
+        // of frames) instead of being descended into here.
+        const bool try_split = desc && gq < prm.split_target;
+        if (__ballot_sync(FULL, try_split) != 0u) {
+            int cp = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) cp += __popc(Pc[k]);
+            const int np = g.sum(cp);
+            const bool sp = try_split && (unsigned)np >= split_min;
+            const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc);
+            if (pushed) {
+                desc = false;
+                ++gq;
+                if (g.leader()) ++cn.don;
+            }
+        }
         bool spill = false;
         if (desc && more) {
             if (d < (int)prm.stack_levels) {
@@ -689,10 +1048,11 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
             }
         }
         if (__ballot_sync(FULL, spill) != 0u) {
-            // stack full: the rest of this frame goes to the queue whole
-            bool whole = false;
-            const int ne = donate<G, K>(g, prm, spill, kKeepNone, P, X, L, pe, rs, S, whole, c_don);
-            if (spill && ne < 0 && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
+            // stack full: the rest of this frame (L is non-empty) goes to the
+            // global ring as it stands, and the group descends without it
+            const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S);
+            if (pushed && g.leader()) ++cn.don;
+            if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
         if (desc) {
 #pragma unroll
@@ -707,30 +1067,166 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
         }
     }
 
-    // ---- reduction: warp, then one atomic per counter per warp
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c_cnt += __shfl_xor_sync(FULL, c_cnt, o);
-        c_nodes += __shfl_xor_sync(FULL, c_nodes, o);
-        c_int += __shfl_xor_sync(FULL, c_int, o);
-        c_dead += __shfl_xor_sync(FULL, c_dead, o);
-        c_hash += __shfl_xor_sync(FULL, c_hash, o);
-        c_don += __shfl_xor_sync(FULL, c_don, o);
-        c_max = max(c_max, __shfl_xor_sync(FULL, c_max, o));
+}
+
+template <int G, int K, bool SMEM, int PIVOT>
+__global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const SearchParams prm)
+{
+    constexpr int WP = G * K;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+
+    const uint32_t n = prm.n;
+    const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
+    uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
+    uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
+    const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
+    local_queue_reset(lq, (blockDim.x / 32u) * (32u / G));
+
+    // ---- prologue: stage the rows (bulk copy), hash terms, histogram
+    if (SMEM) {
+        if (threadIdx.x == 0) mbar_init(&mbar);
+        __syncthreads();
     }
-    if (g.lane == 0) {
-        unsigned long long *o = reinterpret_cast<unsigned long long *>(prm.out);
-        if (c_cnt) atomicAdd(o + MCE_OUT_COUNT, c_cnt);
-        if (c_nodes) atomicAdd(o + MCE_OUT_NODES, c_nodes);
-        if (c_int) atomicAdd(o + MCE_OUT_INTERNAL, c_int);
-        if (c_dead) atomicAdd(o + MCE_OUT_DEAD_ENDS, c_dead);
-        if (c_hash) atomicAdd(o + MCE_OUT_HASH, c_hash);
-        if (c_don) atomicAdd(o + MCE_OUT_DONATIONS, c_don);
-        if (c_max) atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)c_max);
-    }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) hv[i] = mix64((uint64_t)prm.order[i] + 1u);
+    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hist[i] = 0u;
+    bool staged = true;
+    if (SMEM) staged = stage_rows(srows, prm.rows, (uint32_t)rbytes, (uint32_t)__cvta_generic_to_shared(&mbar), 0u);
+    if (!staged && threadIdx.x == 0) set_status(prm.out, prm.ctl, MCE_ETIMEOUT);
+    const bool ok = __syncthreads_and(staged) != 0;
+
+    __shared__ unsigned deg_sum;
+    const unsigned split_min = split_threshold(SMEM ? srows : prm.rows, n, WP, prm.split_min_p, &deg_sum);
+    Counters cn;
+    if (ok) search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : prm.rows, hv, hist, lq, split_min, cn);
+    flush_counters(cn, prm.out);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x)
         if (hist[i]) atomicAdd(reinterpret_cast<unsigned long long *>(prm.out + MCE_OUT_HIST + i), (unsigned long long)hist[i]);
+}
+
+// Batched form: each block takes graphs of its bucket one at a time, most
+// expensive first, and searches each with its own block-local queue region
+// (the same frame ring as the single-graph kernel, private to the block).
+// Per graph: output initialised with the root counted (status kept), rows
+// bulk-copied to shared memory, root frame queued, search, reduction into the
+// graph's own result array.
+template <int G, int K, bool SMEM, int PIVOT>
+__global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchParams bp)
+{
+    constexpr int WP = G * K;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ unsigned cur, root_key;
+
+    unsigned char *region = bp.qbase + (size_t)blockIdx.x * bp.qstride;
+    Ctl *ctl = reinterpret_cast<Ctl *>(region);
+    unsigned *seq = reinterpret_cast<unsigned *>(region + batch_seq_offset());
+    uint32_t *frames = reinterpret_cast<uint32_t *>(region + batch_frames_offset(bp.qcap));
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (SMEM) {
+        if (threadIdx.x == 0) mbar_init(&mbar);
+        __syncthreads();
+    }
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(bp.next, 1u);
+        __syncthreads();
+        const unsigned idx = cur;
+        if (idx >= bp.count) break;
+        const BatchGraph gd = bp.graphs[bp.list[idx]];
+        const uint32_t n = gd.n;
+        const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
+        uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
+        uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
+        const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
+        local_queue_reset(lq, bp.groups_per_block);
+        const bool valid = gd.out[MCE_OUT_STATUS] == 0ull;
+        const bool root = valid && n > 0u;
+
+        for (uint32_t j = threadIdx.x; j < MCE_OUT_WORDS(n); j += blockDim.x) {
+            if (j == MCE_OUT_STATUS) continue;
+            uint64_t v = 0ull;
+            if (j == MCE_OUT_NODES) v = 1ull;
+            if (n > 0u && j == MCE_OUT_INTERNAL) v = 1ull;
+            if (n == 0u && (j == MCE_OUT_COUNT || j == MCE_OUT_HIST)) v = 1ull;
+            if (n == 0u && j == MCE_OUT_HASH) v = mix64(0ull ^ mix64(0ull));
+            gd.out[j] = v;
+        }
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) hv[j] = mix64((uint64_t)gd.order[j] + 1u);
+        for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hist[j] = 0u;
+        for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) seq[j] = (j == 0u && root) ? 1u : j;
+        for (uint32_t w = threadIdx.x; w < (uint32_t)WP; w += blockDim.x) {
+            const uint32_t base = w * 32u;
+            uint32_t pw = 0u;
+            if (n >= base + 32u) pw = FULL;
+            else if (n > base) pw = (1u << (n - base)) - 1u;
+            frames[kFrameHdr + w] = pw;
+            frames[kFrameHdr + WP + w] = 0u;
+        }
+        if (PIVOT == MCE_PIVOT_TOMITA) {
+            if (threadIdx.x == 0) root_key = 0u;
+            __syncthreads();
+            unsigned mine = 0u;
+            for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+                unsigned deg = 0;
+                for (uint32_t w = 0; w < (uint32_t)WP; ++w) deg += __popc(gd.ren[(size_t)v * WP + w]);
+                const unsigned key = ((deg + 1u) << 12) | (4095u - v);
+                mine = key > mine ? key : mine;
+            }
+            atomicMax(&root_key, mine);
+        }
+        bool staged = true;
+        if (SMEM) staged = stage_rows(srows, gd.ren, (uint32_t)rbytes, mb, phase & 1u);
+        ++phase;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned p0 = (PIVOT == MCE_PIVOT_TOMITA && n > 0u) ? (4095u - (root_key & 4095u)) : 0u;
+            frames[0] = (p0 & 0xffffu) | (n << 16);
+            frames[1] = 0u;
+            frames[2] = 0u;
+            frames[3] = 0u;
+            ctl->head = 0u;
+            ctl->abort = 0u;
+            ctl->tail = root ? 1u : 0u;
+            ctl->pending = root ? 1u : 0u;
+            ctl->starving = 0u;
+            if (!staged) {
+                atomicCAS(reinterpret_cast<unsigned long long *>(gd.out + MCE_OUT_STATUS), 0ull,
+                          static_cast<unsigned long long>(static_cast<long long>(MCE_ETIMEOUT)));
+            }
+        }
+        __threadfence();
+        const bool ok = __syncthreads_and(staged) != 0;
+
+        SearchParams prm;
+        prm.n = n;
+        prm.wp = WP;
+        prm.rows = gd.ren;
+        prm.order = gd.order;
+        prm.ctl = ctl;
+        prm.seq = seq;
+        prm.frames = frames;
+        prm.qcap = bp.qcap;
+        prm.fs = bp.fs;
+        prm.out = gd.out;
+        prm.timeout_ns = bp.timeout_ns;
+        prm.total_groups = bp.groups_per_block;
+        prm.pivot_mode = bp.pivot_mode;
+        prm.stack_levels = bp.stack_levels;
+        prm.split_min_p = bp.split_min_p;
+        prm.split_target = bp.split_target;
+        const unsigned split_min = split_threshold(SMEM ? srows : gd.ren, n, WP, bp.split_min_p, &root_key);
+        Counters cn;
+        if (ok) search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : gd.ren, hv, hist, lq, split_min, cn);
+        flush_counters(cn, gd.out);
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x)
+            if (hist[j]) atomicAdd(reinterpret_cast<unsigned long long *>(gd.out + MCE_OUT_HIST + j), (unsigned long long)hist[j]);
+        __syncthreads();
+    }
 }
 
 // Root of Alg. 4 (P = V, X = R = {}) as the first queued frame, empty queue
@@ -783,7 +1279,7 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
             c->tail = 0u;
             c->pending = 0u;
         }
-        c->idle = prm.total_groups;
+        c->starving = 0u;
     }
 }
 

@@ -36,15 +36,38 @@ cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
                                                          smem);
 }
 
+template <int G, int K, bool SMEM, int PIVOT>
+cudaError_t run_batch_t(const BatchParams &bp, const LaunchShape &sh, cudaStream_t s)
+{
+    batch_kernel<G, K, SMEM, PIVOT><<<sh.blocks, sh.threads, sh.smem, s>>>(bp);
+    return cudaGetLastError();
+}
+
+template <int G, int K, bool SMEM, int PIVOT>
+cudaError_t batch_occupancy_t(int threads, size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<G, K, SMEM, PIVOT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<G, K, SMEM, PIVOT>, threads,
+                                                         smem);
+}
+
+template <int G, int K, bool SMEM, int PIVOT>
+SearchImpl impl_t()
+{
+    return {run_search_t<G, K, SMEM, PIVOT>, occupancy_t<G, K, SMEM, PIVOT>, run_batch_t<G, K, SMEM, PIVOT>,
+            batch_occupancy_t<G, K, SMEM, PIVOT>};
+}
+
 template <int G, int K, bool SMEM>
 SearchImpl pick_pivot(int pivot)
 {
     switch (pivot) {
-    case MCE_PIVOT_GREEDY: return {run_search_t<G, K, SMEM, MCE_PIVOT_GREEDY>, occupancy_t<G, K, SMEM, MCE_PIVOT_GREEDY>};
-    case MCE_PIVOT_GREEDY_TX:
-        return {run_search_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>, occupancy_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>};
-    case MCE_PIVOT_TOMITA: return {run_search_t<G, K, SMEM, MCE_PIVOT_TOMITA>, occupancy_t<G, K, SMEM, MCE_PIVOT_TOMITA>};
-    default: return {nullptr, nullptr};
+    case MCE_PIVOT_GREEDY: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY>();
+    case MCE_PIVOT_GREEDY_TX: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>();
+    case MCE_PIVOT_TOMITA: return impl_t<G, K, SMEM, MCE_PIVOT_TOMITA>();
+    default: return {nullptr, nullptr, nullptr, nullptr};
     }
 }
 
@@ -55,7 +78,7 @@ SearchImpl pick(bool smem, int pivot)
     if constexpr (G * K <= 32) {
         if (smem) return pick_pivot<G, K, true>(pivot);
     }
-    if (smem) return {nullptr, nullptr};
+    if (smem) return {nullptr, nullptr, nullptr, nullptr};
     return pick_pivot<G, K, false>(pivot);
 }
 

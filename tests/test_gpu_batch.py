@@ -1,0 +1,106 @@
+"""GPU parity of the batched form: every graph of a batch gives exactly the
+result it gives alone and the oracle's (count, histogram, hash, search-tree
+counters), whatever shapes the batch mixes."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mce():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_00202_gb300 as m
+    m.build()
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mce):
+    c = mce.Context(0)
+    yield c
+    c.close()
+
+
+def _check(got, n, uv, mode="greedy"):
+    ref = oracle.tomita(n, uv)
+    tree = oracle.ordered(n, uv, mode)
+    assert got["status"] == 0
+    assert (got["count"], got["hash"]) == (ref["count"], ref["hash"])
+    assert np.array_equal(got["hist"], ref["hist"])
+    assert (got["nodes"], got["internal"], got["dead_ends"]) == (tree["nodes"], tree["internal"], tree["dead_ends"])
+
+
+def mixed_specs():
+    specs = [(0, synth.empty(0)), (1, synth.empty(1)), (30, synth.gnp(30, 0.5, 1)), (45, synth.moon_moser(8)[:0]),
+             (45, synth.moon_moser(15)[:600]), (64, synth.gnp(64, 0.6, 2)), (100, synth.gnp(100, 0.5, 0)),
+             (129, synth.gnp(129, 0.3, 3)), (200, synth.gnp(200, 0.25, 4)), (256, synth.gnp(256, 0.2, 5)),
+             (300, synth.gnp(300, 0.2, 6)), (512, synth.gnp(512, 0.1, 7)), (700, synth.gnp(700, 0.05, 8)),
+             (1100, synth.gnp(1100, 0.02, 9)), (20, synth.complete(20)), (90, synth.cycle(90))]
+    return specs
+
+
+@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita"])
+def test_mixed_batch_matches_oracle(ctx, mce, mode):
+    specs = mixed_specs()
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    res = mce.enumerate_batch(ctx, graphs, mce.options(pivot=mode))
+    for (n, uv), got in zip(specs, res):
+        _check(got, n, uv, mode)
+    for g in graphs:
+        g.free()
+
+
+def test_batch_equals_alone_and_replays(ctx, mce):
+    specs = [(int(n), synth.gnp(int(n), p, 100 + i)) for i, (n, p) in
+             enumerate([(40, 0.7), (80, 0.5), (150, 0.4), (260, 0.3), (400, 0.2), (500, 0.15)] * 6)]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    alone = [g.enumerate() for g in graphs]
+    b = mce.Batch(ctx, graphs)
+    for _ in range(3):                      # the captured graph replays
+        res = b.run()
+        for a, r in zip(alone, res):
+            assert (a["count"], a["hash"], a["nodes"]) == (r["count"], r["hash"], r["nodes"])
+            assert np.array_equal(a["hist"], r["hist"])
+    b.close()
+    for g in graphs:
+        g.free()
+
+
+@pytest.mark.parametrize("kw", [dict(threads=32), dict(threads=1024), dict(blocks=1, threads=64),
+                                dict(lanes=32, words=1), dict(stack_levels=3, queue_log2=18)])
+def test_batch_launch_shapes(ctx, mce, kw):
+    sizes = (33, 70, 140) if "stack_levels" in kw else (33, 70, 140, 250, 400)
+    specs = [(n, synth.gnp(n, 0.35, 200 + n)) for n in sizes]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    try:
+        res = mce.enumerate_batch(ctx, graphs, mce.options(**kw))
+        for (n, uv), got in zip(specs, res):
+            _check(got, n, uv)
+    finally:
+        for g in graphs:
+            g.free()
+
+
+def test_batch_of_workload_graphs(ctx, mce):
+    """A slice of the 4096-graph batched workload (capped G(n, p))."""
+    specs = synth.batch_graphs(64)
+    graphs = [ctx.load_edges(s.n, s.uv) for s in specs]
+    res = mce.enumerate_batch(ctx, graphs)
+    checked = 0
+    for s, got in zip(specs, res):
+        if synth.expected_maximal_cliques(s.n, s.p) > 2e5 or checked == 24:
+            continue
+        checked += 1
+        ref = oracle.ordered(s.n, s.uv)
+        assert (got["count"], got["hash"], got["nodes"]) == (ref["count"], ref["hash"], ref["nodes"])
+    for g in graphs:
+        g.free()

@@ -1,0 +1,70 @@
+"""GPU parity of the served form (continuous batching): requests submitted
+while others run give exactly their alone results and the oracle's."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mce():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1801_00202_gb300 as m
+    m.build()
+    m.lib()
+    return m
+
+
+def test_mix_equals_alone(mce):
+    ctx = mce.Context(0)
+    specs = [(n, synth.gnp(n, p, 300 + i)) for i, (n, p) in
+             enumerate([(64, 0.6), (100, 0.5), (300, 0.25), (700, 0.1), (1500, 0.03), (2048, 0.02),
+                        (45, 0.9), (128, 0.4), (900, 0.08), (200, 0.35)] * 4)]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    alone = [g.enumerate() for g in graphs]
+    tickets = []
+    for g in graphs:                         # arrive while earlier ones run
+        tickets.append(ctx.submit(g))
+        time.sleep(0.0005)
+    got = [None] * len(tickets)
+    deadline = time.time() + 120
+    while any(x is None for x in got) and time.time() < deadline:
+        for i, t in enumerate(tickets):
+            if got[i] is None:
+                got[i] = ctx.poll(t)
+        time.sleep(0.001)
+    for (n, uv), a, r in zip(specs, alone, got):
+        assert r is not None and r["rc"] == 0
+        assert (r["count"], r["hash"], r["nodes"], r["internal"], r["dead_ends"]) == \
+            (a["count"], a["hash"], a["nodes"], a["internal"], a["dead_ends"])
+        assert np.array_equal(r["hist"], a["hist"])
+    for (n, uv), r in list(zip(specs, got))[:10]:
+        ref = oracle.tomita(n, uv)
+        assert (r["count"], r["hash"]) == (ref["count"], ref["hash"])
+    for g in graphs:
+        g.free()
+    ctx.close()
+
+
+def test_wait_and_small_budget(mce):
+    # a budget that admits only a few requests at a time still serves all
+    ctx = mce.Context(0, mem_budget=256 << 20)
+    specs = [(n, synth.gnp(n, 0.3, 400 + n)) for n in (80, 160, 320, 640, 1000, 80, 160, 320)]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    tickets = [ctx.submit(g) for g in graphs]
+    for (n, uv), t in zip(specs, tickets):
+        r = ctx.wait(t, timeout_ns=60_000_000_000)
+        ref = oracle.ordered(n, uv)
+        assert r["rc"] == 0 and (r["count"], r["hash"], r["nodes"]) == (ref["count"], ref["hash"], ref["nodes"])
+    for g in graphs:
+        g.free()
+    ctx.close()
