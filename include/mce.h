@@ -127,7 +127,11 @@ typedef struct {
 #define MCE_OUT_STATUS     5   /* 0 or a negative MCE_* code (as int64)      */
 #define MCE_OUT_MAX_SIZE   6   /* size of the largest maximal clique         */
 #define MCE_OUT_DONATIONS  7   /* work frames handed between warps           */
-#define MCE_OUT_STEALS     8   /* frames taken from the work queue           */
+#define MCE_OUT_STEALS     8   /* frames taken from a work queue (any level) */
+#define MCE_OUT_GLOBAL     9   /* ... of which from the device-wide queue    */
+#define MCE_OUT_BUSY_NS   10   /* subtree-group time spent holding a frame:
+                                  utilisation = busy / (groups x duration)   */
+#define MCE_OUT_GROUPS    11   /* subtree groups of the launch               */
 #define MCE_OUT_HIST       16
 #define MCE_OUT_WORDS(n)   (MCE_OUT_HIST + (uint64_t)(n) + 1)
 
@@ -266,6 +270,20 @@ int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res);
 int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res);
 
 const char *mce_strerror(int code);
+
+/* ----------------------------------------------------------------------- */
+/* Diagnostics                                                               */
+
+/* Per-block work timeline of the following single-graph searches on this
+ * host thread's current device (NULL / 0 turns it off).  d_buf (device,
+ * caller-owned, zeroed by the caller) is split evenly between the launch's
+ * blocks; each block appends 16-byte records whenever it refreshes its view
+ * of the device-wide queue (about every 2 us while it runs):
+ *   uint64 globaltimer ns, uint16 busy groups of the block, uint16 frames in
+ *   the block ring, uint16 frames in the device-wide queue (saturating),
+ *   uint16 starving blocks (saturating).
+ * Records past a block's share are dropped. */
+int mce_trace_enable(void *d_buf, uint64_t bytes);
 
 #ifdef __cplusplus
 }

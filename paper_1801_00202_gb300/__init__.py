@@ -28,7 +28,7 @@ MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED = 0x1, 0x2, 0x4
 
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
 MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
-MCE_OUT_STEALS = 8
+MCE_OUT_STEALS, MCE_OUT_GLOBAL, MCE_OUT_BUSY_NS, MCE_OUT_GROUPS = 8, 9, 10, 11
 MCE_OUT_HIST = 16
 
 
@@ -99,6 +99,7 @@ _SIGS = {
     "mce_poll": (C.c_int, [_VP, _U64, C.POINTER(Result)]),
     "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
     "mce_strerror": (C.c_char_p, [C.c_int]),
+    "mce_trace_enable": (C.c_int, [_VP, _U64]),
 }
 
 
@@ -189,6 +190,10 @@ def mce_enumerate_device(n, words_per_row, d_rows, opts, d_scratch, scratch_byte
                                       _ptr(d_out), _stream(stream))
 
 
+def mce_trace_enable(d_buf, nbytes: int) -> int:
+    return lib().mce_trace_enable(_ptr(d_buf), nbytes)
+
+
 def decode_out(out, n: int) -> dict:
     """Result dict from a device/host d_out array of MCE_OUT_WORDS(n) uint64."""
     a = np.asarray(out.cpu().numpy() if hasattr(out, "cpu") else out).view(np.uint64)
@@ -196,7 +201,8 @@ def decode_out(out, n: int) -> dict:
             "internal": int(a[MCE_OUT_INTERNAL]), "dead_ends": int(a[MCE_OUT_DEAD_ENDS]),
             "hash": int(a[MCE_OUT_HASH]), "status": int(a[MCE_OUT_STATUS].astype(np.int64)),
             "max_size": int(a[MCE_OUT_MAX_SIZE]), "donations": int(a[MCE_OUT_DONATIONS]),
-            "steals": int(a[MCE_OUT_STEALS]),
+            "steals": int(a[MCE_OUT_STEALS]), "global_steals": int(a[MCE_OUT_GLOBAL]),
+            "busy_ns": int(a[MCE_OUT_BUSY_NS]), "groups": int(a[MCE_OUT_GROUPS]),
             "hist": a[MCE_OUT_HIST:MCE_OUT_HIST + n + 1].copy()}
 
 

@@ -10,6 +10,7 @@
 #include <thread>
 #include <unordered_map>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -27,6 +28,8 @@ struct Config {
     int G = 32, K = 1;
     bool smem = false;
     unsigned threads = 0, blocks = 0;
+    uint32_t stack_levels = 0, stack_offset = 0;
+    size_t smem_bytes = 0;
     uint32_t wp = 32;
     uint32_t qcap = 1024, fs = 0;
     uint32_t total_groups = 0;
@@ -50,6 +53,11 @@ SearchImpl impl_for(int G, int K, bool smem, int pivot)
     switch (G * 8 + K) {
     case 1 * 8 + 1: return search_impl_1_1(smem, pivot);
     case 1 * 8 + 2: return search_impl_1_2(smem, pivot);
+    case 1 * 8 + 4: return search_impl_1_4(smem, pivot);
+    case 2 * 8 + 4: return search_impl_2_4(smem, pivot);
+    case 4 * 8 + 4: return search_impl_4_4(smem, pivot);
+    case 8 * 8 + 4: return search_impl_8_4(smem, pivot);
+    case 16 * 8 + 4: return search_impl_16_4(smem, pivot);
     case 2 * 8 + 1: return search_impl_2_1(smem, pivot);
     case 2 * 8 + 2: return search_impl_2_2(smem, pivot);
     case 4 * 8 + 1: return search_impl_4_1(smem, pivot);
@@ -74,19 +82,57 @@ uint32_t next_pow2(uint64_t x)
 
 size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem) { return search_smem_bytes(n, wp, rows_in_smem); }
 
-// Default subtree width: the narrowest group whose sets still fit one word
-// per lane, one thread per subtree below 65 vertices.
+// Shared-memory stack: as many levels (up to kStackSmemMax) as fit between
+// `base` (rows, hash terms, histogram, block ring) and `limit`.
+void plan_stack_for(uint32_t base, int G, int K, unsigned threads, size_t limit, uint32_t &levels, uint32_t &offset,
+                    size_t &total)
+{
+    offset = (uint32_t)round_up(base, 16);
+    const size_t per_level = (size_t)(threads / 32) * stack_level_words(G, K) * 32 * 4;
+    const size_t avail = limit > offset ? limit - offset : 0;
+    levels = (uint32_t)std::min<size_t>(kStackSmemMax, avail / per_level);
+    total = offset + (size_t)levels * per_level;
+}
+
+// Default subtree shape: up to four words per lane, so that several
+// subtrees share every warp instruction (the search is issue-bound), one
+// thread per subtree up to 64 vertices.
 void default_shape(uint32_t n, int &G, int &K)
 {
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
     if (W <= 1) { G = 1; K = 1; }
     else if (W <= 2) { G = 1; K = 2; }
-    else if (W <= 4) { G = 4; K = 1; }
-    else if (W <= 8) { G = 8; K = 1; }
-    else if (W <= 16) { G = 16; K = 1; }
-    else if (W <= 32) { G = 32; K = 1; }
-    else if (W <= 64) { G = 32; K = 2; }
+    else if (W <= 4) { G = 2; K = 2; }
+    else if (W <= 8) { G = 2; K = 4; }
+    else if (W <= 16) { G = 4; K = 4; }
+    else if (W <= 32) { G = 8; K = 4; }
+    else if (W <= 64) { G = 16; K = 4; }
     else { G = 32; K = 4; }
+}
+
+// Shape for n vertices under the caller's options: forced lanes/words win;
+// otherwise the default, narrowed to two words per lane when the caller asks
+// for more threads per block than four-word shapes allow.
+void pick_shape(uint32_t n, const mce_options &o, int &G, int &K)
+{
+    const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
+    default_shape(n, G, K);
+    if (o.lanes_per_subtree || o.words_per_lane) {
+        if (o.lanes_per_subtree) G = (int)o.lanes_per_subtree;
+        if (o.words_per_lane) K = (int)o.words_per_lane;
+        else K = (int)std::max<uint32_t>(1, (W + G - 1) / G);
+        if (K == 3) K = 4;
+    } else if (o.threads_per_block > 512u && K == 4 && G < 32) {
+        K = 2;
+        G *= 2;
+    }
+}
+
+unsigned default_threads(uint32_t n, int K)
+{
+    const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
+    if (W <= 4) return 256u;
+    return K >= 4 ? 512u : 1024u;
 }
 
 int choose(uint32_t n, const mce_options &o, Config &c)
@@ -95,13 +141,7 @@ int choose(uint32_t n, const mce_options &o, Config &c)
         return MCE_EINVAL;
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
     int G, K;
-    default_shape(n, G, K);
-    if (o.lanes_per_subtree || o.words_per_lane) {
-        if (o.lanes_per_subtree) G = (int)o.lanes_per_subtree;
-        if (o.words_per_lane) K = (int)o.words_per_lane;
-        else K = (int)std::max<uint32_t>(1, (W + G - 1) / G);
-        if (K == 3) K = 4;
-    }
+    pick_shape(n, o, G, K);
     if ((uint32_t)(G * K) < W) return MCE_EINVAL;
     c.impl = impl_for(G, K, false, (int)o.pivot_mode);
     if (!c.impl.run) return MCE_EINVAL;
@@ -120,13 +160,15 @@ int choose(uint32_t n, const mce_options &o, Config &c)
     if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode);
     if (search_smem(n, c.wp, c.smem) > limit) return MCE_EINVAL;
 
-    c.threads = o.threads_per_block ? o.threads_per_block : (K >= 4 ? 512u : 1024u);
+    c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n, K);
     if (c.threads % 32 || c.threads > (K >= 4 ? 512u : 1024u)) return MCE_EINVAL;
+    plan_stack_for((uint32_t)search_smem(n, c.wp, c.smem), c.G, c.K, c.threads, limit, c.stack_levels,
+                   c.stack_offset, c.smem_bytes);
     if (o.blocks) {
         c.blocks = o.blocks;
     } else {
         int per_sm = 0;
-        if (c.impl.occupancy((int)c.threads, search_smem(n, c.wp, c.smem), &per_sm) != cudaSuccess) return MCE_ECUDA;
+        if (c.impl.occupancy((int)c.threads, c.smem_bytes, &per_sm) != cudaSuccess) return MCE_ECUDA;
         if (per_sm < 1) return MCE_ENOMEM;
         c.blocks = (unsigned)(per_sm * sms);
     }
@@ -157,6 +199,38 @@ Layout layout(uint32_t n, const Config &c)
 
 int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErrorMemoryAllocation ? MCE_ENOMEM : MCE_ECUDA); }
 
+}  // namespace
+
+Tuning mce::default_tuning()
+{
+    static const Tuning t = [] {
+        Tuning d{0u, 0u, 4u, 16u, 2000u};  // 0: thresholds by density
+        if (const char *env = std::getenv("MCE_TUNE")) {
+            const char *p = env;
+            while (*p) {
+                char key[32] = {0};
+                unsigned val = 0;
+                int used = 0;
+                if (std::sscanf(p, "%31[a-z_]=%u%n", key, &val, &used) != 2) break;
+                if (!std::strcmp(key, "share_local")) d.share_local = val;
+                else if (!std::strcmp(key, "share_global")) d.share_global = val;
+                else if (!std::strcmp(key, "local_check") && val) d.local_check = val;
+                else if (!std::strcmp(key, "global_check") && val) d.global_check = val;
+                else if (!std::strcmp(key, "refresh_ns")) d.refresh_ns = val;
+                p += used;
+                if (*p == ',') ++p;
+            }
+        }
+        return d;
+    }();
+    return t;
+}
+
+namespace {
+
+thread_local void *g_trace = nullptr;
+thread_local uint64_t g_trace_bytes = 0;
+
 SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char *scratch, const uint32_t *rows,
                     const uint32_t *order, uint64_t *out, const mce_options &o)
 {
@@ -177,6 +251,15 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
     p.stack_levels = o.stack_levels ? std::min<uint32_t>(o.stack_levels, kStackDepth) : kStackDepth;
     p.split_min_p = o.split_min_p;  // 0: by density
     p.split_target = c.qcap / 2;
+    p.stack_smem_levels = c.stack_levels;
+    p.stack_offset = c.stack_offset;
+    p.tune = default_tuning();
+    p.trace = nullptr;
+    p.trace_per_block = 0;
+    if (g_trace && c.blocks) {
+        p.trace = static_cast<unsigned long long *>(g_trace);
+        p.trace_per_block = (uint32_t)std::min<uint64_t>(g_trace_bytes / 16 / c.blocks, 0xffffffffu);
+    }
     return p;
 }
 
@@ -184,7 +267,7 @@ int run_search(uint32_t n, const Config &c, const Layout &L, unsigned char *scra
                const uint32_t *order, uint64_t *out, const mce_options &o, cudaStream_t s)
 {
     SearchParams p = params(n, c, L, scratch, rows, order, out, o);
-    LaunchShape sh{c.blocks, c.threads, search_smem(n, c.wp, c.smem), c.smem};
+    LaunchShape sh{c.blocks, c.threads, c.smem_bytes, c.smem};
     return cuda_code(c.impl.run(p, sh, s));
 }
 
@@ -648,6 +731,7 @@ struct Bucket {
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
     LaunchShape shape{};
     uint32_t qcap = 0, fs = 0, groups = 0;
+    uint32_t stack_levels = 0, stack_offset = 0;
     size_t qstride = 0, list_off = 0, region_off = 0, next_off = 0;
 };
 
@@ -676,9 +760,11 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
         return MCE_EINVAL;
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
         return MCE_ECUDA;
+    const size_t slimit = (size_t)optin - 1024;
 
     mce_batch *b = new (std::nothrow) mce_batch;
     if (!b) return MCE_ENOMEM;
@@ -697,12 +783,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
         b->n[i] = g->n;
         const uint32_t W = std::max<uint32_t>(1, (g->n + 31) / 32);
         int G, K;
-        default_shape(g->n, G, K);
-        if (o.lanes_per_subtree || o.words_per_lane) {
-            if (o.lanes_per_subtree) G = (int)o.lanes_per_subtree;
-            K = o.words_per_lane ? (int)o.words_per_lane : (int)std::max<uint32_t>(1, (W + G - 1) / G);
-            if (K == 3) K = 4;
-        }
+        pick_shape(g->n, o, G, K);
         if ((uint32_t)(G * K) < W || !impl_for(G, K, false, (int)o.pivot_mode).run) { delete b; return MCE_EINVAL; }
         size_t bi = 0;
         while (bi < buckets.size() && !(buckets[bi].G == G && buckets[bi].K == K)) ++bi;
@@ -744,10 +825,14 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     for (Bucket &bk : buckets) {
         std::stable_sort(bk.graphs.begin(), bk.graphs.end(), [&](uint32_t a, uint32_t c2) { return cost[a] > cost[c2]; });
         bk.impl = impl_for(bk.G, bk.K, bk.smem, (int)o.pivot_mode);
-        size_t smem = 0;
-        for (uint32_t i : bk.graphs) smem = std::max(smem, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
+        size_t base = 0;
+        for (uint32_t i : bk.graphs) base = std::max(base, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
         unsigned threads = o.threads_per_block ? o.threads_per_block : 256u;
         if (threads % 32 || threads > (bk.K >= 4 ? 512u : 1024u)) { rc = MCE_EINVAL; break; }
+        // at most 56 KB of stack per block, so that several blocks share an SM
+        size_t smem = 0;
+        plan_stack_for((uint32_t)base, bk.G, bk.K, threads, std::min<size_t>(slimit, base + 56 * 1024),
+                       bk.stack_levels, bk.stack_offset, smem);
         int per_sm = 0;
         if (bk.impl.batch_occupancy((int)threads, smem, &per_sm) != cudaSuccess || per_sm < 1) { rc = MCE_EINVAL; break; }
         unsigned blocks = o.blocks ? o.blocks : (unsigned)(per_sm * sms);
@@ -832,6 +917,9 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
             bp.groups_per_block = bk.groups;
             bp.split_min_p = o.split_min_p;
             bp.split_target = bk.qcap / 2;
+            bp.stack_smem_levels = bk.stack_levels;
+            bp.stack_offset = bk.stack_offset;
+            bp.tune = default_tuning();
             ce = cudaStreamWaitEvent(b->side[i], b->events[0], 0);
             if (ce == cudaSuccess) ce = bk.impl.run_batch(bp, bk.shape, b->side[i]);
             if (ce == cudaSuccess) ce = cudaEventRecord(b->events[i + 1], b->side[i]);
@@ -1192,6 +1280,13 @@ extern "C" int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_res
     const auto limit = std::chrono::nanoseconds(timeout_ns ? timeout_ns : 3600ull * 1000000000ull);
     if (!sv->done_cv.wait_for(lk, limit, [&] { return r->state == 2; })) return MCE_ETIMEOUT;
     return deliver(sv, r, res);
+}
+
+extern "C" int mce_trace_enable(void *d_buf, uint64_t bytes)
+{
+    g_trace = bytes >= 16 ? d_buf : nullptr;
+    g_trace_bytes = g_trace ? bytes : 0;
+    return MCE_OK;
 }
 
 extern "C" const char *mce_strerror(int code)

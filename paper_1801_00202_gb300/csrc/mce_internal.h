@@ -46,13 +46,23 @@ struct LocalHdr {
     // cached global state (refreshed every few microseconds)
     unsigned g_head, g_tail, g_starving, g_abort;
     unsigned long long stamp;
-    unsigned pad[2];
+    unsigned trace_n;     // timeline records written by this block
+    unsigned pad;
 };
 __host__ __device__ inline size_t frame_words(uint32_t wp) { return (8 + 2 * (size_t)wp + 3) / 4 * 4; }
 __host__ __device__ inline size_t local_queue_bytes(uint32_t wp)
 {
     return sizeof(LocalHdr) + kLocalSlots * 4 + (size_t)kLocalSlots * frame_words(wp) * 4;
 }
+
+// Work-distribution knobs (defaults in default_tuning(); MCE_TUNE overrides).
+struct Tuning {
+    uint32_t share_local;   // smallest |P| given to the block ring (0: by density)
+    uint32_t share_global;  // smallest |P| given to the device-wide ring (0: by density)
+    uint32_t local_check;   // busy warps: iterations between block-ring checks
+    uint32_t global_check;  // busy warps: iterations between global checks
+    uint32_t refresh_ns;    // age of a block's cached view of the global ring
+};
 
 struct SearchParams {
     uint32_t n;             // vertices
@@ -71,6 +81,11 @@ struct SearchParams {
     uint32_t stack_levels;  // <= kStackDepth
     uint32_t split_min_p;   // publish new subtrees with |P| >= this ...
     uint32_t split_target;  // ... while the global ring holds fewer frames
+    uint32_t stack_smem_levels;  // explicit-stack levels kept in shared memory
+    uint32_t stack_offset;       // byte offset of the stack region in shared memory
+    unsigned long long *trace;   // optional timeline (2 words per record)
+    uint32_t trace_per_block;    // records per block
+    Tuning tune;
 };
 
 // One graph of a batch (device table entry; pointers into library memory).
@@ -93,6 +108,8 @@ struct BatchParams {
     uint64_t timeout_ns;
     uint32_t pivot_mode, stack_levels, groups_per_block;
     uint32_t split_min_p, split_target;
+    uint32_t stack_smem_levels, stack_offset;
+    Tuning tune;
 };
 
 // Per-block queue region of the batched search: [Ctl | seq | frames]
@@ -122,14 +139,19 @@ struct SearchImpl {
 };
 SearchImpl search_impl_1_1(bool smem, int pivot);
 SearchImpl search_impl_1_2(bool smem, int pivot);
+SearchImpl search_impl_1_4(bool smem, int pivot);
 SearchImpl search_impl_2_1(bool smem, int pivot);
 SearchImpl search_impl_2_2(bool smem, int pivot);
+SearchImpl search_impl_2_4(bool smem, int pivot);
 SearchImpl search_impl_4_1(bool smem, int pivot);
 SearchImpl search_impl_4_2(bool smem, int pivot);
+SearchImpl search_impl_4_4(bool smem, int pivot);
 SearchImpl search_impl_8_1(bool smem, int pivot);
 SearchImpl search_impl_8_2(bool smem, int pivot);
+SearchImpl search_impl_8_4(bool smem, int pivot);
 SearchImpl search_impl_16_1(bool smem, int pivot);
 SearchImpl search_impl_16_2(bool smem, int pivot);
+SearchImpl search_impl_16_4(bool smem, int pivot);
 SearchImpl search_impl_32_1(bool smem, int pivot);
 SearchImpl search_impl_32_2(bool smem, int pivot);
 SearchImpl search_impl_32_4(bool smem, int pivot);
@@ -155,21 +177,35 @@ cudaError_t launch_renumber_batch(const BatchGraph *graphs, uint32_t count, uint
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Tuning in effect for this process: defaults, overridden once from the
+// environment variable MCE_TUNE="key=value,..." (keys as in Tuning).
+Tuning default_tuning();
+
 // Shared-memory layout of the search kernels:
-//   [rows (when staged), padded to 16 B][hv: n x u64][hist: (n + 1) x u32,
-//   padded to 16 B][local frame ring]
+//   [rows (when staged), padded to 16 B][hv: n x u64][hk: (n + 1) x u64]
+//   [hist: (n + 1) x u32, padded to 16 B][local frame ring][stack]
 __host__ __device__ inline size_t smem_rows_bytes(uint32_t n, uint32_t wp, bool rows_in_smem)
 {
     return rows_in_smem ? ((size_t)n * wp * 4 + 15) / 16 * 16 : 0;
 }
 __host__ __device__ inline size_t smem_local_offset(uint32_t n, uint32_t wp, bool rows_in_smem)
 {
-    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + (((size_t)n + 1) * 4 + 15) / 16 * 16;
+    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + ((size_t)n + 1) * 8 +
+           (((size_t)n + 1) * 4 + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem)
 {
     return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp);
 }
+// Explicit-stack words per lane per level for groups of `lanes` lanes with
+// `words` words per lane: P, X and the level's scalars (one word when the
+// group has four or more lanes to spread them over, else four).
+__host__ __device__ inline uint32_t stack_level_words(int lanes, int words)
+{
+    return 2u * (uint32_t)words + (lanes >= 4 ? 1u : 4u);
+}
+// Most levels worth keeping in shared memory (deeper ones use local memory).
+constexpr int kStackSmemMax = 24;
 
 
 }  // namespace mce

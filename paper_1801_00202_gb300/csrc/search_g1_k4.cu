@@ -1,0 +1,3 @@
+// Search kernels with 1 lane(s) per subtree and 4 word(s) per lane.
+#include "search_inst.cuh"
+MCE_DEFINE_SEARCH(1, 4)

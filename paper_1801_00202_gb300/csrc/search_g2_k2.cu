@@ -1,0 +1,3 @@
+// Search kernels with 2 lane(s) per subtree and 2 word(s) per lane.
+#include "search_inst.cuh"
+MCE_DEFINE_SEARCH(2, 2)

@@ -1,0 +1,3 @@
+// Search kernels with 32 lane(s) per subtree and 1 word(s) per lane.
+#include "search_inst.cuh"
+MCE_DEFINE_SEARCH(32, 1)

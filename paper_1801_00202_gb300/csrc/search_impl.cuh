@@ -43,30 +43,39 @@
 namespace mce {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr unsigned kLocalCheck = 4;      // busy warps: iterations between local-ring checks
-constexpr unsigned kGlobalCheck = 16;    // busy warps: iterations between global checks
 constexpr unsigned kCasTries = 1u << 14; // bound of one queue ticket loop
-// Smallest candidate set |P| of a frame worth giving away, per level: a
-// frame is a whole subtree, so tiny ones cost more to move than to expand.
-constexpr int kMinShareLocal = 20;
-constexpr int kMinShareGlobal = 28;
-constexpr uint64_t kRefreshNs = 2000;    // age of the cached global state
 
-// Default split threshold by edge density p = i/40 (i = 1..39): the smallest
-// candidate-set size k whose random subgraph G(k, p) has at least 64 maximal
-// cliques in expectation (sum_j C(k,j) p^C(j,2) (1-p^j)^(k-j) >= 64), so a
-// published subtree carries enough work to pay for the move.
-__constant__ unsigned char kSplitByDensity[39] = {66, 52, 45, 41, 38, 36, 34, 33, 31, 30, 29, 28, 27,
-                                                  26, 25, 24, 24, 23, 23, 22, 21, 21, 21, 20, 20, 20,
-                                                  19, 19, 19, 19, 19, 19, 19, 19, 19, 20, 21, 23, 28};
+// Work-distribution thresholds by edge density p = i/40 (i = 1..39): the
+// smallest candidate-set size k whose random subgraph G(k, p) has at least
+// 256, 2048 or 16384 maximal cliques in expectation
+// (sum_j C(k,j) p^C(j,2) (1-p^j)^(k-j)).  A frame is given to the block ring
+// when its candidate set reaches the first, to the device-wide ring when it
+// reaches the second, and a new subtree is published breadth-first when it
+// reaches the third: what moves must carry enough work to pay for the move,
+// and the further it moves the more work that takes.  The two sharing
+// thresholds are capped by a fraction of n (see density_thresholds).
+__constant__ unsigned short kShareLocalByDensity[39] = {147, 111, 96, 87, 80, 73, 68, 63, 58, 55, 52, 49, 47,
+                                                        44,  42,  41, 39, 37, 36, 35, 33, 32, 31, 30, 29, 29,
+                                                        28,  27,  26, 26, 25, 25, 25, 25, 25, 25, 26, 28, 34};
+__constant__ unsigned short kShareGlobalByDensity[39] = {440, 343, 283, 234, 199, 174, 155, 141, 129, 119, 110,
+                                                         102, 94,  88,  82,  77,  73,  69,  65,  62,  58,  55,
+                                                         53,  50,  48,  46,  44,  42,  41,  39,  38,  37,  36,
+                                                         35,  34,  34,  35,  36,  42};
+__constant__ unsigned short kSplitByDensity[39] = {1363, 907, 651, 515, 433, 376, 329, 290, 257, 230, 208, 189, 173,
+                                                   159,  146, 135, 125, 116, 108, 101, 94,  88,  83,  78,  73,  69,
+                                                   65,   61,  58,  55,  52,  50,  48,  46,  45,  44,  43,  45,  51};
 
-// Split threshold for a block's graph: the caller's value, else the table
-// entry for the density of the staged rows.  Whole block; returns the same
-// value in every thread.
-__device__ __forceinline__ unsigned split_threshold(const uint32_t *rows, uint32_t n, uint32_t wp, uint32_t fixed,
-                                                    unsigned *scratch_u32)
+struct Thresholds {
+    unsigned share_local, share_global, split;
+};
+
+// Thresholds for a block's graph from the density of its rows; non-zero
+// caller values win.  Whole block (barriers inside); every thread gets the
+// same values.
+__device__ __forceinline__ Thresholds density_thresholds(const uint32_t *rows, uint32_t n, uint32_t wp,
+                                                         unsigned fixed_local, unsigned fixed_global,
+                                                         unsigned fixed_split, unsigned *scratch_u32)
 {
-    if (fixed) return fixed;
     if (threadIdx.x == 0) *scratch_u32 = 0u;
     __syncthreads();
     unsigned mine = 0;
@@ -75,11 +84,23 @@ __device__ __forceinline__ unsigned split_threshold(const uint32_t *rows, uint32
     __syncthreads();
     const unsigned deg_sum = *scratch_u32;
     __syncthreads();
-    if (n < 2) return 0xffffffffu;
-    const double pd = (double)deg_sum / ((double)n * (double)(n - 1));
-    int i = (int)(pd * 40.0 + 0.5);
-    i = i < 1 ? 1 : (i > 39 ? 39 : i);
-    return kSplitByDensity[i - 1];
+    Thresholds t{0xffffffffu, 0xffffffffu, 0xffffffffu};
+    if (n >= 2) {
+        const double pd = (double)deg_sum / ((double)n * (double)(n - 1));
+        int i = (int)(pd * 40.0 + 0.5);
+        i = i < 1 ? 1 : (i > 39 ? 39 : i);
+        // The tables assume random graphs; a structured graph (Moon-Moser:
+        // every branching set has three vertices) keeps big subtrees at
+        // much smaller |P|, so a candidate set holding a good share of the
+        // graph also counts as big.
+        t.share_local = min((unsigned)kShareLocalByDensity[i - 1], max(16u, n / 8u));
+        t.share_global = min((unsigned)kShareGlobalByDensity[i - 1], max(20u, n / 4u));
+        t.split = kSplitByDensity[i - 1];
+    }
+    if (fixed_local) t.share_local = fixed_local;
+    if (fixed_global) t.share_global = fixed_global;
+    if (fixed_split) t.split = fixed_split;
+    return t;
 }
 
 // SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014), the mixing step
@@ -200,7 +221,8 @@ struct Grp {
         return anyp(o != 0u);
     }
     // Position of the lowest set bit of the group's set (= the vertex first
-    // in the order), or -1 if the set is empty.
+    // in the order), or -1 if the set is empty.  A whole-warp group takes
+    // one min-reduction; narrower groups a ballot and a shuffle.
     __device__ __forceinline__ int first(const uint32_t (&s)[K]) const
     {
         int loc = -1;
@@ -208,13 +230,37 @@ struct Grp {
         for (int k = K - 1; k >= 0; --k)
             if (s[k]) loc = (int)((gl * K + k) * 32u) + __ffs(s[k]) - 1;
         if (G == 1) return loc;
+        if (G == 32) return (int)__reduce_min_sync(FULL, (unsigned)loc);
         unsigned b = __ballot_sync(FULL, loc >= 0) & gmask;
         int src = b ? (__ffs(b) - 1) : (int)lane;
         int r = __shfl_sync(FULL, loc, src);
         return b ? r : -1;
     }
+    // Emptiness of two sets at once.
+    __device__ __forceinline__ void any2(const uint32_t (&a)[K], const uint32_t (&b)[K], bool &ra, bool &rb) const
+    {
+        uint32_t oa = 0, ob = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            oa |= a[k];
+            ob |= b[k];
+        }
+        if (G == 1) {
+            ra = oa != 0u;
+            rb = ob != 0u;
+        } else if (G == 32) {
+            const unsigned m = __reduce_or_sync(FULL, (oa != 0u ? 1u : 0u) | (ob != 0u ? 2u : 0u));
+            ra = (m & 1u) != 0u;
+            rb = (m & 2u) != 0u;
+        } else {
+            const unsigned ba = __ballot_sync(FULL, oa != 0u), bb = __ballot_sync(FULL, ob != 0u);
+            ra = (ba & gmask) != 0u;
+            rb = (bb & gmask) != 0u;
+        }
+    }
     __device__ __forceinline__ int sum(int x) const
     {
+        if (G == 32) return (int)__reduce_add_sync(FULL, (unsigned)x);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
         return x;
@@ -355,6 +401,7 @@ __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned grou
         q.h->g_starving = 0u;
         q.h->g_abort = 0u;
         q.h->stamp = 0ull;
+        q.h->trace_n = 0u;
     }
 }
 
@@ -480,7 +527,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
 
 // Per-warp result counters (meaningful in group leaders; summed at the end).
 struct Counters {
-    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0;
+    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0, gsteals = 0, busy = 0;
     unsigned max = 0;
 };
 
@@ -497,6 +544,8 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         c.hash += __shfl_xor_sync(FULL, c.hash, o);
         c.don += __shfl_xor_sync(FULL, c.don, o);
         c.steals += __shfl_xor_sync(FULL, c.steals, o);
+        c.gsteals += __shfl_xor_sync(FULL, c.gsteals, o);
+        c.busy += __shfl_xor_sync(FULL, c.busy, o);
         c.max = max(c.max, __shfl_xor_sync(FULL, c.max, o));
     }
     if ((threadIdx.x & 31u) == 0) {
@@ -508,6 +557,8 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         if (c.hash) atomicAdd(o + MCE_OUT_HASH, c.hash);
         if (c.don) atomicAdd(o + MCE_OUT_DONATIONS, c.don);
         if (c.steals) atomicAdd(o + MCE_OUT_STEALS, c.steals);
+        if (c.gsteals) atomicAdd(o + MCE_OUT_GLOBAL, c.gsteals);
+        if (c.busy) atomicAdd(o + MCE_OUT_BUSY_NS, c.busy);
         if (c.max) atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)c.max);
     }
 }
@@ -569,6 +620,114 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Explicit per-group stack of frames.  Levels [0, SL) live in this warp's
+// slice of shared memory, laid out [level][word][lane] so every lane has its
+// own bank; deeper levels live in local memory.  Per level a lane keeps its
+// K words of P and of X plus M "meta" words: with four or more lanes per
+// group, lane j < 4 of the group keeps field j of (pivot|end, |R|, S low,
+// S high) and the fields come back by shuffles; narrower groups keep all
+// four fields in every lane.  |R| and S are the same in every lane.
+template <int G, int K>
+struct Stack {
+    static constexpr int M = (G >= 4) ? 1 : 4;
+    static constexpr int LW = 2 * K + M;
+    uint32_t *sm;  // this lane's column of the warp's slice (kept in a register)
+    int SL;
+    uint32_t (*lw)[LW];  // local-memory levels, indexed by the absolute level
+
+    __device__ __forceinline__ static uint32_t pick(unsigned pe, unsigned rs, uint64_t S, unsigned j)
+    {
+        return j == 0u ? pe : (j == 1u ? rs : (j == 2u ? (uint32_t)S : (uint32_t)(S >> 32)));
+    }
+    __device__ __forceinline__ void put(int d, unsigned gl, const uint32_t (&P)[K], const uint32_t (&X)[K],
+                                        unsigned pe, unsigned rs, uint64_t S)
+    {
+        if (d < SL) {
+            uint32_t *w = sm + (size_t)d * LW * 32;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                w[k * 32] = P[k];
+                w[(K + k) * 32] = X[k];
+            }
+            if (M == 1) {
+                if (gl < 4u) w[2 * K * 32] = pick(pe, rs, S, gl);
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) w[(2 * K + j) * 32] = pick(pe, rs, S, (unsigned)j);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                lw[d][k] = P[k];
+                lw[d][K + k] = X[k];
+            }
+            if (M == 1) {
+                lw[d][2 * K] = pick(pe, rs, S, gl < 4u ? gl : 0u);
+            } else {
+#pragma unroll
+                for (int j = 0; j < M; ++j) lw[d][2 * K + j] = pick(pe, rs, S, (unsigned)j);
+            }
+        }
+    }
+    __device__ __forceinline__ void put_px(int d, const uint32_t (&P)[K], const uint32_t (&X)[K])
+    {
+        if (d < SL) {
+            uint32_t *w = sm + (size_t)d * LW * 32;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                w[k * 32] = P[k];
+                w[(K + k) * 32] = X[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                lw[d][k] = P[k];
+                lw[d][K + k] = X[k];
+            }
+        }
+    }
+    __device__ __forceinline__ void get(int d, uint32_t (&P)[K], uint32_t (&X)[K], uint32_t (&mr)[M])
+    {
+        if (d < SL) {
+            const uint32_t *w = sm + (size_t)d * LW * 32;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                P[k] = w[k * 32];
+                X[k] = w[(K + k) * 32];
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) mr[j] = w[(2 * K + j) * 32];
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                P[k] = lw[d][k];
+                X[k] = lw[d][K + k];
+            }
+#pragma unroll
+            for (int j = 0; j < M; ++j) mr[j] = lw[d][2 * K + j];
+        }
+    }
+};
+
+// Fields of a stack level from the meta words get() returned.  Warp-uniform
+// call (shuffles when the fields are spread over the group's lanes).
+template <int G, int K>
+__device__ __forceinline__ void meta_unpack(const Grp<G, K> &g, const uint32_t (&mr)[Stack<G, K>::M], unsigned &pe,
+                                            unsigned &rs, uint64_t &S)
+{
+    if (Stack<G, K>::M == 1) {
+        pe = __shfl_sync(FULL, mr[0], (int)g.gbase);
+        rs = __shfl_sync(FULL, mr[0], (int)g.gbase + 1);
+        const uint32_t lo = __shfl_sync(FULL, mr[0], (int)g.gbase + 2);
+        const uint32_t hi = __shfl_sync(FULL, mr[0], (int)g.gbase + 3);
+        S = (uint64_t)lo | ((uint64_t)hi << 32);
+    } else {
+        pe = mr[0];
+        rs = mr[Stack<G, K>::M > 1 ? 1 : 0];
+        S = (uint64_t)mr[Stack<G, K>::M > 2 ? 2 : 0] | ((uint64_t)mr[Stack<G, K>::M > 3 ? 3 : 0] << 32);
+    }
+}
+
 // Publish a frame (P, X, pivot|end, |R|, S) as it stands to the global ring
 // (one unit of global pending).  Warp-uniform call; true where it went.
 template <int G, int K>
@@ -617,7 +776,8 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
 // Called by all 32 lanes of every warp.
 template <int G, int K, bool SMEM, int PIVOT>
 __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint32_t *rows, const uint64_t *hv,
-                                            uint32_t *hist, const LocalQ &lq, unsigned split_min, Counters &cn)
+                                            const uint64_t *hk, uint32_t *hist, const LocalQ &lq, const Thresholds th,
+                                            uint32_t *stack_smem, int stack_smem_levels, Counters &cn)
 {
     using Gp = Grp<G, K>;
     constexpr int WP = G * K;
@@ -632,12 +792,16 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     uint64_t S = 0;
     int d = 0, dbase = 0;
     bool work = false;
+    bool lempty = true;  // the current frame's branching set is exhausted
     bool poller = false;
     unsigned gq = 0;  // global ring length last seen
 
-    uint32_t stP[kStackDepth][K], stX[kStackDepth][K];
-    unsigned stPE[kStackDepth], stRS[kStackDepth];
-    uint64_t stS[kStackDepth];
+    using Stk = Stack<G, K>;
+    uint32_t stack_local[kStackDepth][Stk::LW];
+    Stk stk;
+    stk.SL = stack_smem_levels;
+    stk.sm = stack_smem + (size_t)(threadIdx.x >> 5) * (size_t)stack_smem_levels * Stk::LW * 32 + g.lane;
+    stk.lw = stack_local;
 
     uint64_t quiet_since = 0;
     const uint64_t t_start = global_ns();
@@ -649,8 +813,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     auto rowp = [&](int v) -> const uint32_t * { return rows + (size_t)v * WP + g.gl * K; };
 
     // Take (P, X, pivot|end, |R|, S) as this group's frame.
+    uint64_t t_busy = 0;
     auto start_frame = [&]() {
         work = true;
+        lempty = false;
+        if (g.leader()) t_busy = global_ns();
         d = dbase = 0;
         uint32_t rp[K];
         load_row<K, SMEM>(rp, rowp((int)(pe & 0xffffu)));
@@ -663,19 +830,23 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     auto share = [&](bool want, bool local) {
         const bool from_stack = want && d > dbase;
         uint32_t sP[K], sX[K], sL[K], l1[K];
+        uint32_t mr[Stk::M];
+#pragma unroll
+        for (int j = 0; j < Stk::M; ++j) mr[j] = 0u;
         unsigned spe = pe, srs = rs;
         uint64_t sS = S;
+        if (from_stack) stk.get(dbase, sP, sX, mr);
+        {
+            unsigned pe2, rs2;
+            uint64_t S2;
+            meta_unpack<G, K>(g, mr, pe2, rs2, S2);
+            if (from_stack) {
+                spe = pe2;
+                srs = rs2;
+                sS = S2;
+            }
+        }
         if (from_stack) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                sP[k] = stP[dbase][k];
-                sX[k] = stX[dbase][k];
-            }
-            spe = stPE[dbase];
-            if (g.leader()) {
-                srs = stRS[dbase];
-                sS = stS[dbase];
-            }
             uint32_t rp[K];
             load_row<K, SMEM>(rp, rowp((int)(spe & 0xffffu)));
 #pragma unroll
@@ -690,21 +861,23 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         }
         bool whole = false, gave;
         if (local)
-            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, kMinShareLocal, sP, sX, sL, spe, srs, sS, l1,
+            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, (int)th.share_local, sP, sX, sL, spe, srs, sS, l1,
                                             whole, cn.don);
         else
-            gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, kMinShareGlobal, sP, sX, sL, spe, srs, sS,
+            gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, (int)th.share_global, sP, sX, sL, spe, srs, sS,
                                              l1, whole, cn.don);
         if (gave) {
             if (from_stack) {
                 if (whole) {
                     ++dbase;
                 } else {
+                    uint32_t nP[K], nX[K];
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        stP[dbase][k] = sP[k] & ~l1[k];
-                        stX[dbase][k] = sX[k] | l1[k];
+                        nP[k] = sP[k] & ~l1[k];
+                        nX[k] = sX[k] | l1[k];
                     }
+                    stk.put_px(dbase, nP, nX);
                 }
             } else {
 #pragma unroll
@@ -718,38 +891,49 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     };
 
     for (unsigned it = 0;; ++it) {
-        // ---- A: a frame whose branching set is exhausted returns to its parent
-        const bool hasL = g.any(L);
-        if (work && !hasL) {
-            if (d > dbase) {
+        // ---- A: a frame whose branching set is exhausted returns to its
+        // parent (a stacked level always has children left), or the group's
+        // work is done
+        const bool lpop = work && lempty && d > dbase;
+        const bool lfin = work && lempty && d <= dbase;
+        {
+            uint32_t mr[Stk::M];
+#pragma unroll
+            for (int j = 0; j < Stk::M; ++j) mr[j] = 0u;
+            if (lpop) {
                 --d;
+                stk.get(d, P, X, mr);
+            }
+            if (__ballot_sync(FULL, lpop) != 0u) {
+                unsigned pe2, rs2;
+                uint64_t S2;
+                meta_unpack<G, K>(g, mr, pe2, rs2, S2);
+                if (lpop) {
+                    pe = pe2;
+                    rs = rs2;
+                    S = S2;
+                    lempty = false;
+                    uint32_t rp[K];
+                    load_row<K, SMEM>(rp, rowp((int)(pe & 0xffffu)));
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    P[k] = stP[d][k];
-                    X[k] = stX[d][k];
+                    for (int k = 0; k < K; ++k) L[k] = P[k] & ~rp[k] & g.below(k, pe >> 16);
                 }
-                pe = stPE[d];
-                if (g.leader()) {
-                    rs = stRS[d];
-                    S = stS[d];
-                }
-                uint32_t rp[K];
-                load_row<K, SMEM>(rp, rowp((int)(pe & 0xffffu)));
-#pragma unroll
-                for (int k = 0; k < K; ++k) L[k] = P[k] & ~rp[k] & g.below(k, pe >> 16);
-            } else {
-                work = false;
-                if (g.leader()) {
-                    atomicAdd(&lq.h->idle, 1u);
-                    // the last work of the block gives back its unit
-                    if (atomicSub(&lq.h->bwork, 1u) == 1u) atomicSub(&ctl->pending, 1u);
-                }
+            }
+        }
+        if (lfin) {
+            work = false;
+            lempty = false;
+            if (g.leader()) {
+                cn.busy += global_ns() - t_busy;
+                atomicAdd(&lq.h->idle, 1u);
+                // the last work of the block gives back its unit
+                if (atomicSub(&lq.h->bwork, 1u) == 1u) atomicSub(&ctl->pending, 1u);
             }
         }
 
         // ---- B1: the block ring (idle groups take, busy groups refill)
         const unsigned busy_b = __ballot_sync(FULL, work);
-        if (busy_b != FULL || (it % kLocalCheck) == 0u) {
+        if (busy_b != FULL || (it % prm.tune.local_check) == 0u) {
             unsigned lh = 0, lt = 0, li = 0, ld = 0;
             if (g.lane == 0) {
                 lh = vld(&lq.h->head);
@@ -795,9 +979,9 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 
         // ---- B2: the global ring and the end of the search.  Global state is
         // read by the block's polling warp (an all-idle warp) or, at most
-        // every kRefreshNs, by one busy warp, and cached in shared memory.
+        // every tune.refresh_ns, by one busy warp, and cached in shared memory.
         const unsigned busy2 = __ballot_sync(FULL, work);
-        if (busy2 == 0u || (it % kGlobalCheck) == 0u) {
+        if (busy2 == 0u || (it % prm.tune.global_check) == 0u) {
             unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
             bool pol = poller;
             if (g.lane == 0) {
@@ -806,7 +990,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 if (busy2 == 0u && !pol) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
                 const uint64_t now = global_ns();
                 bool refresh = pol;
-                if (!refresh && now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) > kRefreshNs)
+                if (!refresh && now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) > prm.tune.refresh_ns)
                     refresh = atomicCAS(&lq.h->refreshing, 0u, 1u) == 0u;
                 if (refresh) {
                     ab = ld_relaxed(&ctl->abort);
@@ -829,6 +1013,18 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     vst(&lq.h->g_abort, ab);
                     if (ab || pend == 0u) vst(&lq.h->done, 1u);
                     *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) = now;
+                    if (prm.trace) {
+                        const unsigned ti = atomicAdd(&lq.h->trace_n, 1u);
+                        if (ti < prm.trace_per_block) {
+                            const unsigned groups = prm.total_groups / gridDim.x;
+                            const unsigned busy = groups - min(groups, vld(&lq.h->idle));
+                            const unsigned qg = min(tail - head, 65535u), sv = min(starving, 65535u);
+                            unsigned long long *rec = prm.trace + 2ull * ((size_t)blockIdx.x * prm.trace_per_block + ti);
+                            rec[0] = now;
+                            rec[1] = (unsigned long long)busy | ((unsigned long long)min(lt - lh, 65535u) << 16) |
+                                     ((unsigned long long)qg << 32) | ((unsigned long long)sv << 48);
+                        }
+                    }
                     if (now - t_start > 10ull * prm.timeout_ns) set_status(prm.out, ctl, MCE_ETIMEOUT);
                     if (!pol) atomicExch(&lq.h->refreshing, 0u);
                 } else {
@@ -880,6 +1076,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     // an already active block absorbs the frame's unit
                     if (atomicAdd(&lq.h->bwork, 1u) != 0u) atomicSub(&ctl->pending, 1u);
                     ++cn.steals;
+                    ++cn.gsteals;
                 }
                 start_frame();
             }
@@ -913,9 +1110,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             backoff = 32;
         }
 
-        // ---- C: expand one child v = first(L) of every active frame
-        const bool anyL = g.any(L);  // collective: never inside && or ?:
-        const bool act = work && anyL;
+        // ---- C: expand one child v = first(L) of every active frame.  After
+        // A and B every busy group has a non-empty branching set: pops and
+        // queued frames always carry children, and giving work away always
+        // leaves the giver at least one.
+        const bool act = work;
         const int v = g.first(L);
         uint32_t Pc[K], Xc[K];
 #pragma unroll
@@ -932,17 +1131,20 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             g.clear(P, v);  // P <- P \ {v}
             g.set(X, v);    // X <- X u {v}
         }
-        const bool bp = g.any(Pc);
-        const bool bx = g.any(Xc);
+        // first vertices of X' and P' (ChoosePivotOrdered's candidates) also
+        // answer the emptiness tests of the leaf test
+        const int fx = g.first(Xc);
+        const int fp = g.first(Pc);
+        const bool bx = fx >= 0, bp = fp >= 0;
         uint64_t Sc = 0;
+        if (act) Sc = S + hv[v];  // every lane keeps |R| and S
         if (act && g.leader()) {
             ++cn.nodes;
-            Sc = S + hv[v];
             if (!bp) {
                 if (!bx) {  // P u X empty: R u {v} is a maximal clique
                     const unsigned k = rs + 1u;
                     ++cn.cnt;
-                    cn.hash += mix64(Sc ^ mix64((uint64_t)k));
+                    cn.hash += mix64(Sc ^ hk[k]);
                     cn.max = k > cn.max ? k : cn.max;
                     const unsigned old = atomicAdd(&hist[k], 1u);
                     if (old == 0xffffffffu)
@@ -959,10 +1161,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         // ChoosePivotOrdered on the child (P', X')
         int pc;
         if (PIVOT == MCE_PIVOT_GREEDY) {
-            uint32_t sel[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) sel[k] = bx ? Xc[k] : Pc[k];
-            pc = g.first(sel);
+            pc = bx ? fx : fp;
         } else {
             // argmax |P' n N(u)| over X' (TX) or P' u X' (TomitaBB); scanning
             // candidates in increasing position with '>' keeps the earliest
@@ -974,8 +1173,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 for (int k = 0; k < K; ++k) cand[k] = 0u;
             }
             int best = -1;
-            const int firstP = g.first(Pc);
-            pc = (PIVOT == MCE_PIVOT_GREEDY_TX) ? firstP : -1;  // X' empty: first of P'
+            pc = (PIVOT == MCE_PIVOT_GREEDY_TX) ? fp : -1;  // X' empty: first of P'
             for (;;) {
                 uint32_t o = 0;
 #pragma unroll
@@ -1009,39 +1207,33 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 #pragma unroll
             for (int k = 0; k < K; ++k) Lc[k] = Pc[k] & ~r[k];  // L' = P' \ N(p)
         }
-        const bool hasLc = g.any(Lc);
-        const bool more = g.any(L);
+        bool hasLc, more;
+        g.any2(Lc, L, hasLc, more);
         bool desc = inter && hasLc;
         // Breadth-first split of the top of the tree: a new subtree with a
         // large candidate set goes to the global ring (while the ring is short
-        // of frames) instead of being descended into here.
-        const bool try_split = desc && gq < prm.split_target;
-        if (__ballot_sync(FULL, try_split) != 0u) {
+        // of frames; gq is the same in every lane) instead of being descended
+        // into here.
+        const bool split_open = gq < prm.split_target;  // warp-uniform
+        const bool try_split = desc && split_open;
+        bool any_split = false;
+        if (split_open) any_split = __ballot_sync(FULL, try_split) != 0u;
+        if (any_split) {
             int cp = 0;
 #pragma unroll
             for (int k = 0; k < K; ++k) cp += __popc(Pc[k]);
             const int np = g.sum(cp);
-            const bool sp = try_split && (unsigned)np >= split_min;
+            const bool sp = try_split && (unsigned)np >= th.split;
             const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc);
             if (pushed) {
                 desc = false;
-                ++gq;
                 if (g.leader()) ++cn.don;
             }
         }
         bool spill = false;
         if (desc && more) {
             if (d < (int)prm.stack_levels) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    stP[d][k] = P[k];
-                    stX[d][k] = X[k];
-                }
-                stPE[d] = pe;
-                if (g.leader()) {
-                    stRS[d] = rs;
-                    stS[d] = S;
-                }
+                stk.put(d, g.gl, P, X, pe, rs, S);
                 ++d;
             } else {
                 spill = true;
@@ -1054,6 +1246,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (pushed && g.leader()) ++cn.don;
             if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
+        lempty = act && !desc && !more;
         if (desc) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -1080,7 +1273,8 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
     const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
     uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
     uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
+    uint64_t *hk = hv + n;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(hk + n + 1);
     const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
     local_queue_reset(lq, (blockDim.x / 32u) * (32u / G));
 
@@ -1090,6 +1284,7 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) hv[i] = mix64((uint64_t)prm.order[i] + 1u);
+    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hk[i] = mix64((uint64_t)i);
     for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hist[i] = 0u;
     bool staged = true;
     if (SMEM) staged = stage_rows(srows, prm.rows, (uint32_t)rbytes, (uint32_t)__cvta_generic_to_shared(&mbar), 0u);
@@ -1097,9 +1292,13 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
     const bool ok = __syncthreads_and(staged) != 0;
 
     __shared__ unsigned deg_sum;
-    const unsigned split_min = split_threshold(SMEM ? srows : prm.rows, n, WP, prm.split_min_p, &deg_sum);
+    const Thresholds th = density_thresholds(SMEM ? srows : prm.rows, n, WP, prm.tune.share_local,
+                                             prm.tune.share_global, prm.split_min_p, &deg_sum);
+    uint32_t *stack_smem = reinterpret_cast<uint32_t *>(smem_raw + prm.stack_offset);
     Counters cn;
-    if (ok) search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : prm.rows, hv, hist, lq, split_min, cn);
+    if (ok)
+        search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : prm.rows, hv, hk, hist, lq, th, stack_smem,
+                                       (int)prm.stack_smem_levels, cn);
     flush_counters(cn, prm.out);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x)
@@ -1140,7 +1339,8 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchP
         const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
         uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
         uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
-        uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
+        uint64_t *hk = hv + n;
+        uint32_t *hist = reinterpret_cast<uint32_t *>(hk + n + 1);
         const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
         local_queue_reset(lq, bp.groups_per_block);
         const bool valid = gd.out[MCE_OUT_STATUS] == 0ull;
@@ -1156,6 +1356,7 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchP
             gd.out[j] = v;
         }
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) hv[j] = mix64((uint64_t)gd.order[j] + 1u);
+        for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hk[j] = mix64((uint64_t)j);
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hist[j] = 0u;
         for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) seq[j] = (j == 0u && root) ? 1u : j;
         for (uint32_t w = threadIdx.x; w < (uint32_t)WP; w += blockDim.x) {
@@ -1218,9 +1419,18 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchP
         prm.stack_levels = bp.stack_levels;
         prm.split_min_p = bp.split_min_p;
         prm.split_target = bp.split_target;
-        const unsigned split_min = split_threshold(SMEM ? srows : gd.ren, n, WP, bp.split_min_p, &root_key);
+        prm.stack_smem_levels = bp.stack_smem_levels;
+        prm.stack_offset = bp.stack_offset;
+        prm.trace = nullptr;
+        prm.trace_per_block = 0;
+        prm.tune = bp.tune;
+        const Thresholds th = density_thresholds(SMEM ? srows : gd.ren, n, WP, bp.tune.share_local,
+                                                 bp.tune.share_global, bp.split_min_p, &root_key);
         Counters cn;
-        if (ok) search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : gd.ren, hv, hist, lq, split_min, cn);
+        if (ok)
+            search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : gd.ren, hv, hk, hist, lq, th,
+                                           reinterpret_cast<uint32_t *>(smem_raw + bp.stack_offset),
+                                           (int)bp.stack_smem_levels, cn);
         flush_counters(cn, gd.out);
         __syncthreads();
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x)
@@ -1251,6 +1461,7 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
         if (n > 0u && i == MCE_OUT_INTERNAL) v = 1ull;
         if (n == 0u && (i == MCE_OUT_COUNT || i == MCE_OUT_HIST)) v = 1ull;
         if (n == 0u && i == MCE_OUT_HASH) v = mix64(0ull ^ mix64(0ull));
+        if (i == MCE_OUT_GROUPS) v = prm.total_groups;
         prm.out[i] = v;
     }
     if (n > 0u) {

@@ -78,11 +78,11 @@ def test_pivot_rules(ctx, mce, mode, n, p, seed):
     expect_equal(run_host(ctx, mce, n, uv, pivot=mode), n, uv, mode=mode, what=f"{mode} G({n},{p})")
 
 
-SHAPES = [(1, 1), (1, 2), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (16, 1), (16, 2), (32, 1), (32, 2),
-          (32, 4)]
+SHAPES = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4),
+          (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4)]
 
 
-@pytest.mark.parametrize("n,p,seed", [(30, 0.6, 40), (60, 0.5, 41), (120, 0.5, 42)])
+@pytest.mark.parametrize("n,p,seed", [(30, 0.6, 40), (60, 0.5, 41), (120, 0.5, 42), (400, 0.3, 43)])
 def test_every_lane_shape_gives_the_same_tree(ctx, mce, n, p, seed):
     uv = synth.gnp(n, p, seed)
     ref = oracle.tomita(n, uv)
