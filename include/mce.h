@@ -196,6 +196,28 @@ int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_r
                          const mce_options *opts, void *d_scratch, uint64_t scratch_bytes,
                          uint64_t *d_out, void *stream);
 
+/* The whole path like mce_enumerate_device, but with no scratch argument and
+ * no allocation of any kind: the scratch is a fixed area of
+ * MCE_STATIC_SCRATCH_BYTES of device memory inside the library (one per GPU
+ * that loads it, held until the process exits).  The paper has no
+ * counterpart; this exists for callers that may not allocate device memory:
+ * plug-ins whose host framework owns every allocation, request paths that
+ * must not allocate per call, and code running inside a stream capture it
+ * does not own.  The caller still owns d_rows and d_out.
+ *  - The first call on each device looks up the area's address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call reuses the same area; what must start from a known state is
+ *    re-initialised by each call, but calls whose work overlaps on the GPU
+ *    race on the area: do not issue overlapping calls (other streams, other
+ *    host threads) on one device.
+ *  - MCE_ENOMEM when the options need more scratch than the area holds
+ *    (mce_scratch_bytes(n, opts) > MCE_STATIC_SCRATCH_BYTES); the default
+ *    options fit for every n <= MCE_NMAX. */
+#define MCE_STATIC_SCRATCH_BYTES (32u << 20)
+int mce_enumerate_device_static(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+                                const mce_options *opts, uint64_t *d_out, void *stream);
+
 /* ----------------------------------------------------------------------- */
 /* Host-level API: handles, host buffers, batching and serving.             */
 

@@ -83,6 +83,7 @@ _SIGS = {
     "mce_search": (C.c_int, [_U32, _VP, _VP, C.POINTER(Options), _VP, _U64, _VP, _VP]),
     "mce_search_words": (_U32, [_U32, C.POINTER(Options)]),
     "mce_enumerate_device": (C.c_int, [_U32, _U32, _VP, C.POINTER(Options), _VP, _U64, _VP, _VP]),
+    "mce_enumerate_device_static": (C.c_int, [_U32, _U32, _VP, C.POINTER(Options), _VP, _VP]),
     "mce_ctx_create": (C.c_int, [C.c_int, _U64, _VP, C.POINTER(_VP)]),
     "mce_ctx_destroy": (None, [_VP]),
     "mce_load_edges": (C.c_int, [_VP, _U32, _VP, _U64, C.POINTER(_VP)]),
@@ -192,6 +193,16 @@ def mce_enumerate_device(n, words_per_row, d_rows, opts, d_scratch, scratch_byte
 
 def mce_trace_enable(d_buf, nbytes: int) -> int:
     return lib().mce_trace_enable(_ptr(d_buf), nbytes)
+
+
+MCE_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def mce_enumerate_device_static(n, words_per_row, d_rows, opts, d_out, stream=None) -> int:
+    """The whole path with the library's fixed scratch area: nothing is
+    allocated, for callers that may not allocate device memory."""
+    return lib().mce_enumerate_device_static(n, words_per_row, _ptr(d_rows), _opt(opts), _ptr(d_out),
+                                             _stream(stream))
 
 
 def decode_out(out, n: int) -> dict:
