@@ -14,9 +14,13 @@ Usage:
 Prints one JSON line on rank 0.  ``value`` is maximal cliques per second over
 all ranks (each rank runs its own replica: the plain form does not shard).
 ``e2e`` is the same metric through the handle API from pinned host memory
-(mce_load_edges + mce_enumerate + mce_graph_free).  ``--impl reference``
-times the CPU oracle (Bron-Kerbosch with the Tomita pivot) on bounded samples
-of the same graph on the host cores.
+(mce_load_edges + mce_enumerate + mce_graph_free).  ``forms`` holds the
+batched form (4096 graphs of uneven size in one captured launch,
+mce_batch_launch) and the served form (a Poisson request stream through
+mce_submit / mce_poll: graphs/s and p50/p99 latency), each beside the plain
+form (one mce_enumerate call per graph) on the same graphs.  ``--impl
+reference`` times the CPU oracle (Bron-Kerbosch with the Tomita pivot) on
+bounded samples of the same graph on the host cores.
 """
 from __future__ import annotations
 
@@ -69,6 +73,19 @@ ALU_PEAK_OPS = SMS * 4 * 32 * SM_MHZ * 1e6
 SMEM_PEAK_BPS = SMS * 128 * SM_MHZ * 1e6
 ORACLE_SAMPLE_NODES = 1_500_000     # per reference step
 BASELINE_SAMPLE_NODES = 5_000_000   # cpu_baseline leg (about 10-30 s)
+# Batched form: 4096 G(n, p), n uniform in [32, 512], p uniform in [0.2, 0.8],
+# seeds 0..4095, (n, p) redrawn while E[maximal cliques] > 1e6.  Served form:
+# Poisson stream of G(n, p), n log-uniform in [64, 2048], p uniform in
+# [0.1, 0.9], same cap, arrivals at SERVE_LOAD x the capacity measured on the
+# warm-up requests (saturating), then a second pass at LATENCY_LOAD x capacity.
+BATCH_GRAPHS = 4096
+SERVE_LOAD, LATENCY_LOAD = 1.2, 0.7
+# DRAM bytes (read + write) of one search-kernel launch, from a one-pass ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel built
+# from sources with this fingerprint; reported only while the sources match.
+KERNEL_SOURCES = ("search_impl.cuh", "search_inst.cuh", "mce_internal.h", "capi.cu")
+TRAFFIC = {"fingerprint": "672725da20369b99", "workload": "gnp_1000_0.3_s1", "bytes": 705_790 + 8_700,
+           "profile": "profiles/search_kernel_gnp1000_dram.md"}
 
 
 def words(n: int) -> int:
@@ -120,6 +137,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1801_00202_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    if TRAFFIC["workload"] == GOLDEN_KEY and TRAFFIC["fingerprint"] == kernel_fingerprint():
+        return TRAFFIC["bytes"]
+    return None
+
+
 def golden():
     p = os.path.join(ROOT, "tests", "golden", "config_results.json")
     if os.path.exists(p):
@@ -143,6 +175,171 @@ def cpu_baseline(uv, max_nodes: int) -> dict:
             "sample": f"Bron-Kerbosch with the Tomita pivot on the same graph, first {r['nodes']} search nodes "
                       f"({r['count']} maximal cliques, {dt:.1f} s on one host core)",
             "nodes_per_s": r["nodes"] / dt}
+
+
+# ---------------------------------------------------------------------------
+# Batched and served forms
+
+def _gen_batch(i: int):
+    g = synth.batch_graph(i)
+    return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
+
+
+def _gen_served(r: int):
+    g = synth.served_graph(r)
+    return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
+
+
+def generate_forms(args):
+    """Build the batched and served graphs on all host cores (spawned pool,
+    before any CUDA call); bitset rows come back."""
+    import multiprocessing as mp
+    total = args.served_warmup + args.served_requests
+    cores = max(1, min(os.cpu_count() or 1, 32))
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        batch = pool.map(_gen_batch, range(args.batch_graphs), chunksize=32)
+        served = pool.map(_gen_served, range(total), chunksize=64)
+    return batch, served, {"cores": cores, "seconds": time.perf_counter() - t}
+
+
+def _work(results, ns):
+    """Algorithmic lane-ops and row bytes (6W and 8W per search node)."""
+    ops = sum(6 * words(n) * r["nodes"] for r, n in zip(results, ns))
+    return ops, 8 * ops // 6
+
+
+def _rates(graphs, cliques, nodes, ops, row_bytes, seconds):
+    return {"graphs_per_s": graphs / seconds, "cliques_per_s": cliques / seconds, "nodes_per_s": nodes / seconds,
+            "alu_frac": ops / seconds / ALU_PEAK_OPS, "smem_frac": row_bytes / seconds / SMEM_PEAK_BPS}
+
+
+def _same(a, b) -> bool:
+    return (a["count"] == b["count"] and a["hash"] == b["hash"] and a["nodes"] == b["nodes"]
+            and np.array_equal(a["hist"], b["hist"]))
+
+
+def plain_pass(mce, torch, graphs, opts):
+    """Plain form: one mce_enumerate call (whole path, result to host) per
+    graph, back to back."""
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = [g.enumerate(opts) for g in graphs]
+    return res, time.perf_counter() - t
+
+
+def batched_form(mce, torch, ctx, s, specs, opts, args, flush_l2):
+    graphs = [ctx.load_bitset(n, rows) for n, _, _, rows in specs]
+    ns = [n for n, _, _, _ in specs]
+    t = time.perf_counter()
+    b = mce.Batch(ctx, graphs, opts)
+    plan_s = time.perf_counter() - t
+    for _ in range(max(1, args.warmup // 3)):
+        b.run()
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    evs = [(mk(), mk()) for _ in range(args.batch_steps)]
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        flush_l2()
+        e0.record(s)
+        b.launch()
+        e1.record(s)
+    res = b.results()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    plain, plain_s = plain_pass(mce, torch, graphs, opts)
+    b.close()
+    for g in graphs:
+        g.free()
+    sec = statistics.mean(ms) / 1e3
+    cliques, nodes = sum(r["count"] for r in res), sum(r["nodes"] for r in res)
+    ops, rb = _work(res, ns)
+    out = {"workload": f"{len(ns)} G(n,p), n uniform [32,512], p uniform [0.2,0.8], seeds 0..{len(ns) - 1}, "
+                       f"(n,p) redrawn while E[maximal cliques] > 1e6",
+           "graphs": len(ns), "acceptance": len(ns) / sum(d for _, _, d, _ in specs),
+           "mean_n": float(np.mean(ns)), "cliques": cliques, "nodes": nodes,
+           "steps": args.batch_steps, "ms_per_step": statistics.mean(ms), "plan_and_capture_s": plan_s,
+           "batched": _rates(len(ns), cliques, nodes, ops, rb, sec),
+           "plain": _rates(len(ns), cliques, nodes, ops, rb, plain_s),
+           "plain_note": "one mce_enumerate per graph, back to back (wall clock, results read per graph)",
+           "status_ok": all(r["status"] == 0 for r in res),
+           "batched_equals_plain": all(_same(a, c) for a, c in zip(res, plain)),
+           "launches_per_step": "one CUDA graph: a batched ordering kernel, a batched renumbering "
+                                "kernel and one persistent search kernel per subtree shape"}
+    out["speedup_graphs_per_s"] = out["batched"]["graphs_per_s"] / out["plain"]["graphs_per_s"]
+    return out
+
+
+def _open_loop(ctx, graphs, arrivals, opts):
+    """Submit graph i at arrivals[i] (s from the start), poll the oldest
+    requests; latency = submit delay + the library's submit-to-done time."""
+    R = len(graphs)
+    lat = [0.0] * R
+    res = [None] * R
+    pend = []           # (index, ticket, submit time)
+    nxt = done = 0
+    t0 = time.perf_counter()
+    while done < R:
+        now = time.perf_counter() - t0
+        while nxt < R and arrivals[nxt] <= now:
+            ts = time.perf_counter() - t0
+            pend.append((nxt, ctx.submit(graphs[nxt], opts), ts))
+            nxt += 1
+        keep = []
+        for k, (i, tk, ts) in enumerate(pend):
+            if k >= 64:
+                keep.extend(pend[k:])
+                break
+            r = ctx.poll(tk)
+            if r is None:
+                keep.append((i, tk, ts))
+                continue
+            res[i] = r
+            lat[i] = (ts - arrivals[i]) + r["total_ms"] / 1e3
+            done += 1
+        pend = keep
+    finish = max(a + l for a, l in zip(arrivals, lat))
+    return res, lat, finish - arrivals[0]
+
+
+def served_form(mce, torch, ctx, specs, opts, args):
+    graphs = [ctx.load_bitset(n, rows) for n, _, _, rows in specs]
+    ns = [n for n, _, _, _ in specs]
+    W = args.served_warmup
+    warm, timed = graphs[:W], graphs[W:]
+    # warm-up, closed loop: everything submitted at once -> capacity
+    t = time.perf_counter()
+    tickets = [ctx.submit(g, opts) for g in warm]
+    for tk in tickets:
+        ctx.wait(tk)
+    capacity = len(warm) / (time.perf_counter() - t)
+    out = {"workload": f"Poisson stream of G(n,p), n log-uniform [64,2048], p uniform [0.1,0.9], "
+                       f"(n,p) redrawn while E[maximal cliques] > 1e6; {W} warm-up + {len(timed)} timed requests",
+           "requests": len(timed), "warmup_requests": W,
+           "acceptance": len(specs) / sum(d for _, _, d, _ in specs), "mean_n": float(np.mean(ns[W:])),
+           "capacity_closed_loop_graphs_per_s": capacity}
+    for name, load in (("saturating", SERVE_LOAD), ("latency", LATENCY_LOAD)):
+        arr = synth.served_arrivals(len(timed), load * capacity)
+        arr = arr - arr[0]
+        res, lat, span = _open_loop(ctx, timed, arr, opts)
+        cliques, nodes = sum(r["count"] for r in res), sum(r["nodes"] for r in res)
+        ops, rb = _work(res, ns[W:])
+        lat_ms = np.array(lat) * 1e3
+        out[name] = {"offered_graphs_per_s": load * capacity, "load": load,
+                     **_rates(len(timed), cliques, nodes, ops, rb, span),
+                     "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                     "mean_ms": float(lat_ms.mean()), "status_ok": all(r["rc"] == 0 for r in res)}
+        if name == "saturating":
+            first = res
+    k = min(args.plain_sample, len(timed))
+    plain, plain_s = plain_pass(mce, torch, timed[:k], opts)
+    ops, rb = _work(plain, ns[W:W + k])
+    out["plain"] = _rates(k, sum(r["count"] for r in plain), sum(r["nodes"] for r in plain), ops, rb, plain_s)
+    out["plain_note"] = f"one mce_enumerate per request, back to back, first {k} timed requests"
+    out["served_equals_plain"] = all(_same(a, c) for a, c in zip(first[:k], plain))
+    out["speedup_graphs_per_s"] = out["saturating"]["graphs_per_s"] / out["plain"]["graphs_per_s"]
+    for g in graphs:
+        g.free()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -176,6 +373,9 @@ def run_reference(args):
 
 
 def run_ours(args):
+    forms_in = None
+    if not args.no_forms and int(os.environ.get("RANK", "0")) == 0:
+        forms_in = generate_forms(args)     # host cores, before any CUDA call
     import torch
 
     import paper_1801_00202_gb300 as mce
@@ -282,6 +482,17 @@ def run_ours(args):
     if rank != 0:
         dist.destroy_process_group()
         return 0
+    forms = None
+    if forms_in is not None:
+        batch_specs, served_specs, gen = forms_in
+        fctx = mce.Context(local, stream=s)
+        fclk = ClockSampler(local)
+        fclk.start()
+        forms = {"batched": batched_form(mce, torch, fctx, s, batch_specs, mce.options(), args, flush_l2)}
+        forms["served"] = served_form(mce, torch, fctx, served_specs, mce.options(), args)
+        forms["clocks"] = fclk.stop()
+        forms["generation"] = gen
+        fctx.close()
 
     count, nodes = res["count"], res["nodes"]
     value = world * args.steps * count / (total_ms / 1e3)
@@ -308,7 +519,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "search_kernel",
                      "achieved": ops / (search_avg / 1e3) / 1e12, "peak": ALU_PEAK_OPS / 1e12,
                      "unit": "Tops/s (32-bit lane ops)", "frac": ops / (search_avg / 1e3) / ALU_PEAK_OPS,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz",
+                     "traffic": measured_traffic(), "traffic_source": TRAFFIC["profile"],
+                     "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz",
                      "ops_per_node": 6 * W, "nodes_per_launch": nodes},
         "roofline_smem": {"achieved": smem_bytes / (search_avg / 1e3) / 1e9, "peak": SMEM_PEAK_BPS / 1e9,
                           "unit": "GB/s", "frac": smem_bytes / (search_avg / 1e3) / SMEM_PEAK_BPS,
@@ -322,6 +534,7 @@ def run_ours(args):
             "api": "mce_load_edges (pinned host edge list) + mce_enumerate + mce_graph_free"},
         "gpu_launches": 5 * args.steps + (0 if args.no_e2e else 6 * args.steps),
         "clocks": clk,
+        "forms": forms,
     })
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(uv, BASELINE_SAMPLE_NODES)
@@ -340,6 +553,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--batch-graphs", type=int, default=BATCH_GRAPHS)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--served-requests", type=int, default=20000)
+    ap.add_argument("--served-warmup", type=int, default=2000)
+    ap.add_argument("--plain-sample", type=int, default=4000,
+                    help="served requests also run through the plain form for the comparison")
     # launch-shape overrides (0 = the library's choice)
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--words", type=int, default=0)

@@ -29,7 +29,8 @@ its instances are not available, so seeded G(n, p) stands in for them):
 * ``moon_moser_deleted(k, frac, seed)``: the same with round(frac * m) edges
   removed, chosen uniformly without replacement by a partial Fisher-Yates
   shuffle driven by the seed's stream.
-* ``batch_params`` / ``served_requests``: the multi-graph workloads, with
+* ``batch_graph(s)`` / ``served_graph`` / ``served_requests``: the multi-graph
+  workloads (one stream per graph, so any graph can be built alone), with
   (n, p) redrawn while the expected number of maximal cliques exceeds a cap.
 """
 from __future__ import annotations
@@ -259,26 +260,26 @@ def _capped_params(rng: SplitMix64, draw, cap: float):
             return n, p, draws
 
 
-def batch_graphs(count: int = 4096, cap: float = 1e6, first_seed: int = 0,
-                 n_lo: int = 32, n_hi: int = 512, p_lo: float = 0.2, p_hi: float = 0.8):
-    """Batched workload: graph i uses seed first_seed + i.
-
+def batch_graph(i: int, cap: float = 1e6, first_seed: int = 0,
+                n_lo: int = 32, n_hi: int = 512, p_lo: float = 0.2, p_hi: float = 0.8) -> GraphSpec:
+    """Graph i of the batched workload, from its own stream seeded first_seed + i:
     n = n_lo + (next() mod (n_hi - n_lo + 1)), p = p_lo + (p_hi - p_lo) * u,
     redrawn from the same stream while E[mu](n, p) > cap; the edges follow on
-    the same stream.
-    """
+    the same stream."""
     def draw(rng):
         n = n_lo + int(rng.next() % (n_hi - n_lo + 1))
         p = p_lo + (p_hi - p_lo) * rng.uniform()
         return n, p
 
-    out = []
-    for i in range(count):
-        seed = first_seed + i
-        rng = SplitMix64(seed)
-        n, p, draws = _capped_params(rng, draw, cap)
-        out.append(GraphSpec(i, seed, n, p, draws, gnp_from_stream(n, p, rng)))
-    return out
+    seed = first_seed + i
+    rng = SplitMix64(seed)
+    n, p, draws = _capped_params(rng, draw, cap)
+    return GraphSpec(i, seed, n, p, draws, gnp_from_stream(n, p, rng))
+
+
+def batch_graphs(count: int = 4096, cap: float = 1e6, first_seed: int = 0, **kw):
+    """The batched workload: graphs 0 .. count-1 of ``batch_graph``."""
+    return [batch_graph(i, cap, first_seed, **kw) for i in range(count)]
 
 
 @dataclass
@@ -288,15 +289,19 @@ class Request:
     spec: GraphSpec
 
 
-def served_requests(count: int, rate_per_s: float, cap: float = 1e6, seed: int = 5,
-                    n_lo: int = 64, n_hi: int = 2048, p_lo: float = 0.1, p_hi: float = 0.9):
-    """Served workload: Poisson arrivals (exponential gaps from the stream
-    seeded ``seed``) of G(n, p) requests, n = round(exp(U[ln n_lo, ln n_hi])),
-    p ~ U[p_lo, p_hi], capped like ``batch_graphs``.  Request r's graph uses
-    seed (seed << 32) + r."""
+def served_arrivals(count: int, rate_per_s: float, seed: int = 5) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: cumulative exponential gaps of
+    mean 1 / rate_per_s drawn from the stream seeded ``seed``."""
     arrivals = SplitMix64(seed)
     gaps = -np.log1p(-arrivals.uniform_block(count)) / rate_per_s
-    t = np.cumsum(gaps)
+    return np.cumsum(gaps)
+
+
+def served_graph(r: int, cap: float = 1e6, seed: int = 5,
+                 n_lo: int = 64, n_hi: int = 2048, p_lo: float = 0.1, p_hi: float = 0.9) -> GraphSpec:
+    """Request r's graph, from the stream seeded (seed << 32) + r:
+    n = round(exp(U[ln n_lo, ln n_hi])), p ~ U[p_lo, p_hi], capped like
+    ``batch_graph``."""
     lo, hi = math.log(n_lo), math.log(n_hi)
 
     def draw(rng):
@@ -304,10 +309,14 @@ def served_requests(count: int, rate_per_s: float, cap: float = 1e6, seed: int =
         p = p_lo + (p_hi - p_lo) * rng.uniform()
         return n, p
 
-    out = []
-    for r in range(count):
-        s = (seed << 32) + r
-        rng = SplitMix64(s)
-        n, p, draws = _capped_params(rng, draw, cap)
-        out.append(Request(r, float(t[r]), GraphSpec(r, s, n, p, draws, gnp_from_stream(n, p, rng))))
-    return out
+    s = (seed << 32) + r
+    rng = SplitMix64(s)
+    n, p, draws = _capped_params(rng, draw, cap)
+    return GraphSpec(r, s, n, p, draws, gnp_from_stream(n, p, rng))
+
+
+def served_requests(count: int, rate_per_s: float, cap: float = 1e6, seed: int = 5, **kw):
+    """Served workload: Poisson arrivals (``served_arrivals``) of the
+    requests ``served_graph`` draws."""
+    t = served_arrivals(count, rate_per_s, seed)
+    return [Request(r, float(t[r]), served_graph(r, cap, seed, **kw)) for r in range(count)]
