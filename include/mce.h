@@ -84,8 +84,14 @@ extern "C" {
 #define MCE_ORDER_IDENTITY   0x1u  /* skip the maximum-degree-first ordering
                                       (Section 4.2): the input order is the
                                       search order                            */
-#define MCE_LIST             0x2u  /* also return the cliques (host API only) */
-#define MCE_LIST_SORTED      0x4u  /* sort each clique and the listing        */
+#define MCE_LIST             0x2u  /* also return the cliques: mce_enumerate
+                                      only (device-level calls, batches and
+                                      served requests: MCE_ENOTIMPL); each
+                                      clique's labels ascending, cliques in
+                                      no particular order                   */
+#define MCE_LIST_SORTED      0x4u  /* MCE_LIST with the cliques in
+                                      lexicographic order (the problem's
+                                      output, Section 2: all maximal cliques) */
 
 typedef struct {
     uint32_t pivot_mode;        /* MCE_PIVOT_*                                */
@@ -232,11 +238,15 @@ typedef struct {
     uint64_t *hist;               /* caller-owned, hist[k] for k < hist_cap  */
     uint32_t hist_cap;
     uint32_t _pad;
-    uint32_t *list_ids;           /* caller-owned, original labels           */
+    uint32_t *list_ids;           /* caller-owned host array of list_cap
+                                     labels: the members of every clique    */
     uint64_t list_cap;
-    uint64_t *list_off;           /* CSR offsets, count + 1 entries          */
+    uint64_t *list_off;           /* caller-owned host array of list_off_cap
+                                     CSR offsets: clique i is list_ids[
+                                     list_off[i] .. list_off[i+1]), count + 1
+                                     entries are written                    */
     uint64_t list_off_cap;
-    uint64_t list_ids_needed;
+    uint64_t list_ids_needed;     /* out: sum of the clique sizes           */
     double kernel_ms, total_ms;
 } mce_result;
 
@@ -258,7 +268,14 @@ void mce_graph_free(mce_graph *g);
 
 /* Enumerate one graph (plain form).  `res` is in/out: hist and list buffers
  * are caller-owned; counters are filled.  MCE_ETRUNC if hist_cap <=
- * max_size or the listing does not fit (counters still valid). */
+ * max_size or the listing does not fit (counters and list_ids_needed still
+ * valid: a caller can ask with zero capacities, then allocate list_ids_needed
+ * labels and count + 1 offsets and call again).  Listing (MCE_LIST): the
+ * search records each maximal clique where Alg. 4 reports it (a node whose P
+ * and X are empty); frames that move between warps carry R as a bitset; the
+ * records become the CSR listing on the device before the copy to the host.
+ * MCE_ENOMEM if the device records of a listing that fits the caller's
+ * buffers do not fit in device memory. */
 int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
 
 /* Batched form.  mce_batch_create plans a batch of loaded graphs once:

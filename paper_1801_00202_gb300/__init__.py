@@ -314,17 +314,49 @@ class Graph:
     close = free
     __del__ = free
 
-    def enumerate(self, opts: Options | None = None, raise_on_error: bool = True) -> dict:
+    def enumerate(self, opts: Options | None = None, raise_on_error: bool = True,
+                  list_cap: int | None = None, off_cap: int | None = None) -> dict:
+        """mce_enumerate.  With MCE_LIST / MCE_LIST_SORTED in opts.flags the
+        result also holds the listing ("list_ids", "list_off": CSR, original
+        labels, each clique ascending; MCE_LIST_SORTED also orders the
+        cliques lexicographically).  Without capacities, a first call learns
+        the sizes (MCE_ETRUNC) and a second one lists."""
+        listing = opts is not None and (opts.flags & (MCE_LIST | MCE_LIST_SORTED)) != 0
         hist = np.zeros(self.n + 1, dtype=np.uint64)
         r = Result()
         r.hist = hist.ctypes.data_as(C.POINTER(C.c_uint64))
         r.hist_cap = hist.size
+        ids = off = None
+        if listing:
+            if list_cap is None or off_cap is None:
+                probe = self.enumerate(opts, raise_on_error=False, list_cap=0, off_cap=0)
+                if probe["rc"] not in (0, MCE_ETRUNC):
+                    if raise_on_error:
+                        _check(probe["rc"], "mce_enumerate")
+                    return probe
+                list_cap, off_cap = int(probe["list_ids_needed"]), int(probe["count"]) + 1
+            ids = np.zeros(max(list_cap, 1), dtype=np.uint32)
+            off = np.zeros(max(off_cap, 1), dtype=np.uint64)
+            r.list_ids = ids.ctypes.data_as(C.POINTER(C.c_uint32))
+            r.list_cap = list_cap
+            r.list_off = off.ctypes.data_as(C.POINTER(C.c_uint64))
+            r.list_off_cap = off_cap
         rc = lib().mce_enumerate(self.handle, _opt(opts), C.byref(r))
         if raise_on_error:
             _check(rc, "mce_enumerate")
-        return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
-                "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
-                "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}
+        out = {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
+               "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
+               "kernel_ms": r.kernel_ms, "total_ms": r.total_ms, "list_ids_needed": r.list_ids_needed}
+        if listing and rc == 0:
+            out["list_off"] = off[:r.count + 1].copy()
+            out["list_ids"] = ids[:r.list_ids_needed].copy()
+        return out
+
+
+def cliques(res: dict) -> list:
+    """The listing of an enumerate() result as a list of label arrays."""
+    off, ids = res["list_off"], res["list_ids"]
+    return [ids[int(off[i]):int(off[i + 1])] for i in range(len(off) - 1)]
 
 
 def _results_array(ns):

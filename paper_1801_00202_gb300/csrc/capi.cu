@@ -34,6 +34,7 @@ struct Config {
     uint32_t qcap = 1024, fs = 0;
     uint32_t total_groups = 0;
     int pivot = 0;
+    bool list = false;  // frames carry R (clique listing)
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -48,29 +49,21 @@ mce_options defaults(const mce_options *o)
     return d;
 }
 
-SearchImpl impl_for(int G, int K, bool smem, int pivot)
+SearchImpl impl_for(int G, int K, bool smem, int pivot, bool list = false)
 {
+#define MCE_IMPL_CASE(g, k)                                                                                \
+    case g * 8 + k:                                                                                        \
+        return list ? search_list_impl_##g##_##k(smem, pivot) : search_impl_##g##_##k(smem, pivot);
     switch (G * 8 + K) {
-    case 1 * 8 + 1: return search_impl_1_1(smem, pivot);
-    case 1 * 8 + 2: return search_impl_1_2(smem, pivot);
-    case 1 * 8 + 4: return search_impl_1_4(smem, pivot);
-    case 2 * 8 + 4: return search_impl_2_4(smem, pivot);
-    case 4 * 8 + 4: return search_impl_4_4(smem, pivot);
-    case 8 * 8 + 4: return search_impl_8_4(smem, pivot);
-    case 16 * 8 + 4: return search_impl_16_4(smem, pivot);
-    case 2 * 8 + 1: return search_impl_2_1(smem, pivot);
-    case 2 * 8 + 2: return search_impl_2_2(smem, pivot);
-    case 4 * 8 + 1: return search_impl_4_1(smem, pivot);
-    case 4 * 8 + 2: return search_impl_4_2(smem, pivot);
-    case 8 * 8 + 1: return search_impl_8_1(smem, pivot);
-    case 8 * 8 + 2: return search_impl_8_2(smem, pivot);
-    case 16 * 8 + 1: return search_impl_16_1(smem, pivot);
-    case 16 * 8 + 2: return search_impl_16_2(smem, pivot);
-    case 32 * 8 + 1: return search_impl_32_1(smem, pivot);
-    case 32 * 8 + 2: return search_impl_32_2(smem, pivot);
-    case 32 * 8 + 4: return search_impl_32_4(smem, pivot);
+        MCE_IMPL_CASE(1, 1) MCE_IMPL_CASE(1, 2) MCE_IMPL_CASE(1, 4)
+        MCE_IMPL_CASE(2, 1) MCE_IMPL_CASE(2, 2) MCE_IMPL_CASE(2, 4)
+        MCE_IMPL_CASE(4, 1) MCE_IMPL_CASE(4, 2) MCE_IMPL_CASE(4, 4)
+        MCE_IMPL_CASE(8, 1) MCE_IMPL_CASE(8, 2) MCE_IMPL_CASE(8, 4)
+        MCE_IMPL_CASE(16, 1) MCE_IMPL_CASE(16, 2) MCE_IMPL_CASE(16, 4)
+        MCE_IMPL_CASE(32, 1) MCE_IMPL_CASE(32, 2) MCE_IMPL_CASE(32, 4)
     default: return {nullptr, nullptr, nullptr, nullptr};
     }
+#undef MCE_IMPL_CASE
 }
 
 uint32_t next_pow2(uint64_t x)
@@ -80,7 +73,12 @@ uint32_t next_pow2(uint64_t x)
     return (uint32_t)p;
 }
 
-size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem) { return search_smem_bytes(n, wp, rows_in_smem); }
+size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false)
+{
+    return search_smem_bytes(n, wp, rows_in_smem, list);
+}
+
+constexpr uint32_t kListFlags = MCE_LIST | MCE_LIST_SORTED;
 
 // Shared-memory stack: as many levels (up to kStackSmemMax) as fit between
 // `base` (rows, hash terms, histogram, block ring) and `limit`.
@@ -143,7 +141,8 @@ int choose(uint32_t n, const mce_options &o, Config &c)
     int G, K;
     pick_shape(n, o, G, K);
     if ((uint32_t)(G * K) < W) return MCE_EINVAL;
-    c.impl = impl_for(G, K, false, (int)o.pivot_mode);
+    c.list = (o.flags & kListFlags) != 0u;
+    c.impl = impl_for(G, K, false, (int)o.pivot_mode, c.list);
     if (!c.impl.run) return MCE_EINVAL;
     c.G = G;
     c.K = K;
@@ -156,13 +155,13 @@ int choose(uint32_t n, const mce_options &o, Config &c)
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return MCE_ECUDA;
     const size_t limit = (size_t)optin - 1024;  // static shared memory + slack
 
-    c.smem = c.wp <= 32 && search_smem(n, c.wp, true) <= limit;
-    if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode);
-    if (search_smem(n, c.wp, c.smem) > limit) return MCE_EINVAL;
+    c.smem = c.wp <= 32 && search_smem(n, c.wp, true, c.list) <= limit;
+    if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode, c.list);
+    if (search_smem(n, c.wp, c.smem, c.list) > limit) return MCE_EINVAL;
 
     c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n, K);
     if (c.threads % 32 || c.threads > (K >= 4 ? 512u : 1024u)) return MCE_EINVAL;
-    plan_stack_for((uint32_t)search_smem(n, c.wp, c.smem), c.G, c.K, c.threads, limit, c.stack_levels,
+    plan_stack_for((uint32_t)search_smem(n, c.wp, c.smem, c.list), c.G, c.K, c.threads, limit, c.stack_levels,
                    c.stack_offset, c.smem_bytes);
     if (o.blocks) {
         c.blocks = o.blocks;
@@ -175,7 +174,7 @@ int choose(uint32_t n, const mce_options &o, Config &c)
     c.total_groups = c.blocks * (c.threads / 32) * (32 / G);
     c.qcap = next_pow2(std::max<uint64_t>(1024, 4ull * c.total_groups + 256));
     if (o.queue_log2) c.qcap = std::max<uint32_t>(c.qcap, 1u << o.queue_log2);
-    c.fs = (uint32_t)frame_words(c.wp);
+    c.fs = (uint32_t)frame_words(c.wp, c.list);
     return MCE_OK;
 }
 
@@ -232,7 +231,7 @@ thread_local void *g_trace = nullptr;
 thread_local uint64_t g_trace_bytes = 0;
 
 SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char *scratch, const uint32_t *rows,
-                    const uint32_t *order, uint64_t *out, const mce_options &o)
+                    const uint32_t *order, uint64_t *out, const mce_options &o, const ListParams *lp)
 {
     SearchParams p{};
     p.n = n;
@@ -260,13 +259,15 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
         p.trace = static_cast<unsigned long long *>(g_trace);
         p.trace_per_block = (uint32_t)std::min<uint64_t>(g_trace_bytes / 16 / c.blocks, 0xffffffffu);
     }
+    p.lst = lp ? *lp : ListParams{};
     return p;
 }
 
 int run_search(uint32_t n, const Config &c, const Layout &L, unsigned char *scratch, const uint32_t *rows,
-               const uint32_t *order, uint64_t *out, const mce_options &o, cudaStream_t s)
+               const uint32_t *order, uint64_t *out, const mce_options &o, cudaStream_t s,
+               const ListParams *lp = nullptr)
 {
-    SearchParams p = params(n, c, L, scratch, rows, order, out, o);
+    SearchParams p = params(n, c, L, scratch, rows, order, out, o, lp);
     LaunchShape sh{c.blocks, c.threads, c.smem_bytes, c.smem};
     return cuda_code(c.impl.run(p, sh, s));
 }
@@ -309,15 +310,18 @@ extern "C" int mce_renumber(uint32_t n, uint32_t words_per_row, const uint32_t *
 extern "C" uint32_t mce_search_words(uint32_t n, const mce_options *opts)
 {
     Config c;
-    if (n > MCE_NMAX || choose(n, defaults(opts), c) != MCE_OK) return 0;
+    const mce_options o = defaults(opts);
+    if (n > MCE_NMAX || (o.flags & kListFlags) || choose(n, o, c) != MCE_OK) return 0;
     return c.wp;
 }
 
 extern "C" int mce_scratch_bytes(uint32_t n, const mce_options *opts, uint64_t *bytes)
 {
     if (!bytes || n > MCE_NMAX) return MCE_EINVAL;
+    const mce_options o = defaults(opts);
+    if (o.flags & kListFlags) return MCE_ENOTIMPL;  // listing: host API only
     Config c;
-    int rc = choose(n, defaults(opts), c);
+    int rc = choose(n, o, c);
     if (rc) return rc;
     *bytes = layout(n, c).total;
     return MCE_OK;
@@ -330,6 +334,7 @@ extern "C" int mce_search(uint32_t n, const uint32_t *d_rows_renum, const uint32
     if (reinterpret_cast<uintptr_t>(d_scratch) % 256 || reinterpret_cast<uintptr_t>(d_rows_renum) % 16)
         return MCE_EINVAL;
     const mce_options o = defaults(opts);
+    if (o.flags & kListFlags) return MCE_ENOTIMPL;  // listing: host API only
     Config c;
     int rc = choose(n, o, c);
     if (rc) return rc;
@@ -339,20 +344,14 @@ extern "C" int mce_search(uint32_t n, const uint32_t *d_rows_renum, const uint32
                       (cudaStream_t)stream);
 }
 
-extern "C" int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
-                                    const mce_options *opts, void *d_scratch, uint64_t scratch_bytes,
-                                    uint64_t *d_out, void *stream)
+namespace {
+
+// The whole path (validate, order, renumber, search) for a chosen
+// configuration; lp non-null lists the cliques (host API).
+int enumerate_device_impl(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows, const mce_options &o,
+                          const Config &c, const Layout &L, unsigned char *scr, uint64_t *d_out, cudaStream_t s,
+                          const ListParams *lp)
 {
-    if (n > MCE_NMAX || !d_out || !d_scratch || (n && !d_rows) || words_per_row < (n + 31) / 32) return MCE_EINVAL;
-    if (reinterpret_cast<uintptr_t>(d_scratch) % 256) return MCE_EINVAL;
-    const mce_options o = defaults(opts);
-    Config c;
-    int rc = choose(n, o, c);
-    if (rc) return rc;
-    const Layout L = layout(n, c);
-    if (scratch_bytes < L.total) return MCE_ENOMEM;
-    cudaStream_t s = (cudaStream_t)stream;
-    unsigned char *scr = static_cast<unsigned char *>(d_scratch);
     uint32_t *order = reinterpret_cast<uint32_t *>(scr + L.order);
     uint32_t *rows = reinterpret_cast<uint32_t *>(scr + L.rows);
     cudaError_t e = cudaMemsetAsync(d_out + MCE_OUT_STATUS, 0, sizeof(uint64_t), s);
@@ -361,7 +360,26 @@ extern "C" int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const ui
         e = (o.flags & MCE_ORDER_IDENTITY) ? launch_identity(n, order, s) : launch_order(n, words_per_row, d_rows, order, s);
     if (e == cudaSuccess) e = launch_renumber(n, words_per_row, d_rows, order, c.wp, rows, s);
     if (e != cudaSuccess) return cuda_code(e);
-    return run_search(n, c, L, scr, rows, order, d_out, o, s);
+    return run_search(n, c, L, scr, rows, order, d_out, o, s, lp);
+}
+
+}  // namespace
+
+extern "C" int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
+                                    const mce_options *opts, void *d_scratch, uint64_t scratch_bytes,
+                                    uint64_t *d_out, void *stream)
+{
+    if (n > MCE_NMAX || !d_out || !d_scratch || (n && !d_rows) || words_per_row < (n + 31) / 32) return MCE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_scratch) % 256) return MCE_EINVAL;
+    const mce_options o = defaults(opts);
+    if (o.flags & kListFlags) return MCE_ENOTIMPL;  // listing: host API only
+    Config c;
+    int rc = choose(n, o, c);
+    if (rc) return rc;
+    const Layout L = layout(n, c);
+    if (scratch_bytes < L.total) return MCE_ENOMEM;
+    return enumerate_device_impl(n, words_per_row, d_rows, o, c, L, static_cast<unsigned char *>(d_scratch), d_out,
+                                 (cudaStream_t)stream, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,25 +659,133 @@ extern "C" int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *
 }
 
 namespace {
+
+// Device memory of one listing search: control words, chunk fill counts,
+// per-group path and base R, and the record chunks.
+struct ListArea {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    ListParams prm{};
+};
+
+int list_alloc(mce_ctx *ctx, uint32_t n, const Config &c, const mce_result *res, ListArea &la, cudaStream_t s)
+{
+    const uint64_t groups = c.total_groups;
+    const uint32_t cw = std::max<uint32_t>(2048u, 2u * next_pow2((uint64_t)n + 2u));
+    // room for the caller's capacity twice over (chunk tails stay unused) plus
+    // one chunk in every group's hands, within 2^32 words and a third of the
+    // free memory
+    auto sat_add = [](uint64_t x, uint64_t y) { return x + y < x ? ~0ull : x + y; };
+    uint64_t want = sat_add(res->list_cap, res->list_off_cap);
+    want = sat_add(want, want);
+    want = sat_add(want, groups * cw);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MCE_ECUDA;
+    uint64_t cap_words = std::min<uint64_t>((1ull << 32) - cw, free_b / 3 / 4);
+    if (ctx->budget) {
+        const uint64_t used = ctx->used.load();
+        cap_words = std::min<uint64_t>(cap_words, used < ctx->budget ? (ctx->budget - used) / 2 / 4 : 0);
+    }
+    const uint64_t chunks = std::max<uint64_t>(1, std::min(want, cap_words) / cw);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = round_up(off, 256);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t o_ctl = take(256), o_fill = take(chunks * 4), o_path = take(groups * n * 2 + 2),
+                 o_base = take(groups * c.wp * 4), o_rec = take(chunks * (uint64_t)cw * 4);
+    la.bytes = round_up(off, 256);
+    int rc = dalloc(ctx, &la.mem, la.bytes, s);
+    if (rc != MCE_OK) return rc;
+    unsigned char *m = static_cast<unsigned char *>(la.mem);
+    la.prm.next_chunk = reinterpret_cast<unsigned *>(m + o_ctl);
+    la.prm.overflow = reinterpret_cast<unsigned *>(m + o_ctl + 128);
+    la.prm.fill = reinterpret_cast<uint32_t *>(m + o_fill);
+    la.prm.path = reinterpret_cast<uint16_t *>(m + o_path);
+    la.prm.base = reinterpret_cast<uint32_t *>(m + o_base);
+    la.prm.rec = reinterpret_cast<uint32_t *>(m + o_rec);
+    la.prm.n_chunks = (uint32_t)chunks;
+    la.prm.chunk_words = cw;
+    return cuda_code(cudaMemsetAsync(m, 0, o_path, s));  // control words and fill counts
+}
+
+// CSR listing from a finished listing search (result words h) into the
+// caller's host buffers.
+int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d_order,
+                 const std::vector<uint64_t> &h, bool sorted, mce_result *res, cudaStream_t s)
+{
+    const uint64_t count = h[MCE_OUT_COUNT];
+    uint64_t ids = 0;
+    for (uint32_t k = 0; k <= n; ++k) ids += (uint64_t)k * h[MCE_OUT_HIST + k];
+    res->list_ids_needed = ids;
+    unsigned ctl[2] = {0u, 0u};
+    cudaError_t e = cudaMemcpyAsync(&ctl[0], la.prm.next_chunk, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl[1], la.prm.overflow, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return MCE_ECUDA;
+    const bool fits = res->list_off && res->list_off_cap >= count + 1 && (ids == 0 || (res->list_ids && res->list_cap >= ids));
+    if (!fits) return MCE_ETRUNC;
+    if (ctl[1]) return MCE_ENOMEM;  // the caller's buffers fit, the device records did not
+    if (n == 0) {                   // the empty set, reported by the root
+        res->list_off[0] = res->list_off[1] = 0;
+        return MCE_OK;
+    }
+    ListJob j{};
+    j.rec = la.prm.rec;
+    j.fill = la.prm.fill;
+    j.chunks = std::min<uint32_t>(ctl[0], la.prm.n_chunks);
+    j.chunk_words = la.prm.chunk_words;
+    j.order = d_order;
+    j.n = n;
+    j.max_size = (uint32_t)h[MCE_OUT_MAX_SIZE];
+    j.count = count;
+    j.ids = ids;
+    j.sorted = sorted;
+    if (sorted && count > 0xffffffffull) return MCE_ENOTIMPL;
+    const size_t tb = list_temp_bytes(count, ids, j.chunks, sorted);
+    const size_t ib = round_up(std::max<uint64_t>(ids, 1) * 4, 256), ob = round_up((count + 1) * 8, 256);
+    void *mem = nullptr;
+    int rc = dalloc(ctx, &mem, ib + ob + tb, s);
+    if (rc != MCE_OK) return rc;
+    unsigned char *m = static_cast<unsigned char *>(mem);
+    j.ids_out = reinterpret_cast<uint32_t *>(m);
+    j.off_out = reinterpret_cast<uint64_t *>(m + ib);
+    j.temp = m + ib + ob;
+    j.temp_bytes = tb;
+    e = list_build(j, s);
+    if (e == cudaSuccess && ids) e = cudaMemcpyAsync(res->list_ids, j.ids_out, ids * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res->list_off, j.off_out, (count + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(ctx, mem, ib + ob + tb, s);
+    return e == cudaSuccess ? MCE_OK : MCE_ECUDA;
+}
+
 int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0)
 {
     mce_ctx *ctx = g->ctx;
-    if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
-    uint64_t sbytes = 0;
-    int rc = mce_scratch_bytes(g->n, &o, &sbytes);
+    const bool listing = (o.flags & kListFlags) != 0u;
+    Config c;
+    int rc = choose(g->n, o, c);
     if (rc) return rc;
+    const Layout L = layout(g->n, c);
+    const uint64_t sbytes = L.total;
     const size_t obytes = MCE_OUT_WORDS(g->n) * 8;
     void *scr = nullptr;
     uint64_t *d_out = nullptr;
+    ListArea la;
     rc = dalloc(ctx, &scr, sbytes);
     if (rc == MCE_OK) rc = dalloc(ctx, (void **)&d_out, obytes);
+    if (rc == MCE_OK && listing) rc = list_alloc(ctx, g->n, c, res, la, ctx->stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<uint64_t> h(MCE_OUT_WORDS(g->n), 0);
     if (rc == MCE_OK) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, ctx->stream);
-        rc = mce_enumerate_device(g->n, g->w, g->d_rows, &o, scr, sbytes, d_out, ctx->stream);
+        rc = enumerate_device_impl(g->n, g->w, g->d_rows, o, c, L, static_cast<unsigned char *>(scr), d_out, ctx->stream,
+                                   listing ? &la.prm : nullptr);
         cudaEventRecord(e1, ctx->stream);
         if (rc == MCE_OK) {
             cudaError_t e = cudaMemcpyAsync(h.data(), d_out, obytes, cudaMemcpyDeviceToHost, ctx->stream);
@@ -671,14 +797,22 @@ int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chr
     if (rc == MCE_OK && e0 && e1) cudaEventElapsedTime(&kms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    const bool ran = rc == MCE_OK;
+    if (ran) {
+        rc = fill_result(h, g->n, res);
+        res->kernel_ms = kms;
+        if (listing && rc == MCE_OK) {
+            const uint32_t *d_order = reinterpret_cast<const uint32_t *>(static_cast<unsigned char *>(scr) + L.order);
+            rc = list_deliver(ctx, g->n, la, d_order, h, (o.flags & MCE_LIST_SORTED) != 0u, res, ctx->stream);
+        }
+    }
+    if (la.mem) dfree(ctx, la.mem, la.bytes, ctx->stream);
     dfree(ctx, d_out, obytes);
     dfree(ctx, scr, sbytes);
-    if (rc != MCE_OK) {
+    if (!ran) {
         cudaStreamSynchronize(ctx->stream);
         return rc;
     }
-    rc = fill_result(h, g->n, res);
-    res->kernel_ms = kms;
     res->total_ms = ms_since(t0);
     return rc;
 }

@@ -15,6 +15,7 @@ namespace mce {
 //   [1] |R|
 //   [2] S(R) low word, [3] S(R) high word   (running clique hash sum)
 //   [4] graph slot (batched and served forms), [5..7] unused
+// and, when cliques are listed, the bitset R after P and X.
 constexpr int kFrameHdr = 8;
 
 // Levels of the per-group explicit stack (local memory).  Deeper paths spill
@@ -49,11 +50,30 @@ struct LocalHdr {
     unsigned trace_n;     // timeline records written by this block
     unsigned pad;
 };
-__host__ __device__ inline size_t frame_words(uint32_t wp) { return (8 + 2 * (size_t)wp + 3) / 4 * 4; }
-__host__ __device__ inline size_t local_queue_bytes(uint32_t wp)
+__host__ __device__ inline size_t frame_words(uint32_t wp, bool list = false)
 {
-    return sizeof(LocalHdr) + kLocalSlots * 4 + (size_t)kLocalSlots * frame_words(wp) * 4;
+    return (8 + (list ? 3 : 2) * (size_t)wp + 3) / 4 * 4;
 }
+__host__ __device__ inline size_t local_queue_bytes(uint32_t wp, bool list = false)
+{
+    return sizeof(LocalHdr) + kLocalSlots * 4 + (size_t)kLocalSlots * frame_words(wp, list) * 4;
+}
+
+// Clique listing (MCE_LIST).  Every group appends, at each maximal clique it
+// reports, a record [0x80000000 | k, pos_1 .. pos_k] (positions in the search
+// order) to a chunk of the record buffer it claimed; the clique's members are
+// the R of the frame the group last took (its bitset in `base`, its size
+// `rsb`) plus the vertices the group added on its way down (`path`, indexed
+// by |R|), plus the leaf vertex.  Frames that move between groups carry R.
+struct ListParams {
+    uint32_t *rec;          // n_chunks * chunk_words words; null: no listing
+    uint32_t *fill;         // words used in each chunk (zeroed before the search)
+    unsigned *next_chunk;   // chunk claim counter (zeroed)
+    unsigned *overflow;     // set when a record found no chunk (zeroed)
+    uint16_t *path;         // total_groups * n entries
+    uint32_t *base;         // total_groups * wp words
+    uint32_t n_chunks, chunk_words;
+};
 
 // Work-distribution knobs (defaults in default_tuning(); MCE_TUNE overrides).
 struct Tuning {
@@ -86,6 +106,7 @@ struct SearchParams {
     unsigned long long *trace;   // optional timeline (2 words per record)
     uint32_t trace_per_block;    // records per block
     Tuning tune;
+    ListParams lst;              // clique listing (lst.rec null: off)
 };
 
 // One graph of a batch (device table entry; pointers into library memory).
@@ -155,6 +176,25 @@ SearchImpl search_impl_16_4(bool smem, int pivot);
 SearchImpl search_impl_32_1(bool smem, int pivot);
 SearchImpl search_impl_32_2(bool smem, int pivot);
 SearchImpl search_impl_32_4(bool smem, int pivot);
+// Listing variants (run/occupancy only; no batched form).
+SearchImpl search_list_impl_1_1(bool smem, int pivot);
+SearchImpl search_list_impl_1_2(bool smem, int pivot);
+SearchImpl search_list_impl_1_4(bool smem, int pivot);
+SearchImpl search_list_impl_2_1(bool smem, int pivot);
+SearchImpl search_list_impl_2_2(bool smem, int pivot);
+SearchImpl search_list_impl_2_4(bool smem, int pivot);
+SearchImpl search_list_impl_4_1(bool smem, int pivot);
+SearchImpl search_list_impl_4_2(bool smem, int pivot);
+SearchImpl search_list_impl_4_4(bool smem, int pivot);
+SearchImpl search_list_impl_8_1(bool smem, int pivot);
+SearchImpl search_list_impl_8_2(bool smem, int pivot);
+SearchImpl search_list_impl_8_4(bool smem, int pivot);
+SearchImpl search_list_impl_16_1(bool smem, int pivot);
+SearchImpl search_list_impl_16_2(bool smem, int pivot);
+SearchImpl search_list_impl_16_4(bool smem, int pivot);
+SearchImpl search_list_impl_32_1(bool smem, int pivot);
+SearchImpl search_list_impl_32_2(bool smem, int pivot);
+SearchImpl search_list_impl_32_4(bool smem, int pivot);
 
 
 // Preprocessing kernels (prep.cu).
@@ -177,6 +217,24 @@ cudaError_t launch_renumber_batch(const BatchGraph *graphs, uint32_t count, uint
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Listing post-pass (listing.cu): record chunks of a finished listing search
+// -> CSR listing (off[count + 1], ids) in original labels, each clique in
+// ascending order and, when `sorted`, the cliques in lexicographic order.
+struct ListJob {
+    const uint32_t *rec, *fill;  // record buffer and per-chunk fill (search output)
+    uint32_t chunks, chunk_words;  // chunks claimed (<= n_chunks), chunk size
+    const uint32_t *order;       // position -> original label
+    uint32_t n, max_size;
+    uint64_t count, ids;         // cliques and member ids (from the histogram)
+    uint32_t *ids_out;           // device, ids entries
+    uint64_t *off_out;           // device, count + 1 entries
+    bool sorted;
+    void *temp;                  // list_temp_bytes(count, ids, chunks, sorted) bytes
+    size_t temp_bytes;
+};
+size_t list_temp_bytes(uint64_t count, uint64_t ids, uint32_t chunks, bool sorted);
+cudaError_t list_build(const ListJob &j, cudaStream_t s);
+
 // Tuning in effect for this process: defaults, overridden once from the
 // environment variable MCE_TUNE="key=value,..." (keys as in Tuning).
 Tuning default_tuning();
@@ -193,9 +251,9 @@ __host__ __device__ inline size_t smem_local_offset(uint32_t n, uint32_t wp, boo
     return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + ((size_t)n + 1) * 8 +
            (((size_t)n + 1) * 4 + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem)
+__host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false)
 {
-    return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp);
+    return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp, list);
 }
 // Explicit-stack words per lane per level for groups of `lanes` lanes with
 // `words` words per lane: P, X and the level's scalars (one word when the

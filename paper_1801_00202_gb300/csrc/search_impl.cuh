@@ -421,7 +421,8 @@ template <int G, int K, bool LOCAL>
 __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchParams &prm, const LocalQ &lq,
                                              bool pred, bool allow_whole, int min_p, const uint32_t (&P)[K],
                                              const uint32_t (&X)[K], const uint32_t (&L)[K], unsigned pe,
-                                             unsigned rs, uint64_t S, uint32_t (&l1)[K], bool &whole, uint64_t &c_don)
+                                             unsigned rs, uint64_t S, bool list, const uint32_t (&R)[K],
+                                             uint32_t (&l1)[K], bool &whole, uint64_t &c_don)
 {
     constexpr int WP = G * K;
     int cl = 0, cp = 0;
@@ -482,11 +483,12 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
     for (int k = 0; k < K; ++k) l1[k] = got ? (L[k] & g.below(k, (unsigned)split)) : 0u;
     if (got) {
         if (LOCAL) {
-            volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * frame_words(WP);
+            volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * frame_words(WP, list);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 fr[kFrameHdr + g.gl * K + k] = P[k];
                 fr[kFrameHdr + WP + g.gl * K + k] = X[k];
+                if (list) fr[kFrameHdr + 2 * WP + g.gl * K + k] = R[k];
             }
             if (g.leader()) {
                 fr[0] = npe;
@@ -501,6 +503,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
             for (int k = 0; k < K; ++k) {
                 __stcg(fr + kFrameHdr + g.gl * K + k, P[k]);
                 __stcg(fr + kFrameHdr + WP + g.gl * K + k, X[k]);
+                if (list) __stcg(fr + kFrameHdr + 2 * WP + g.gl * K + k, R[k]);
             }
             if (g.leader()) {
                 __stcg(fr + 0, npe);
@@ -728,12 +731,13 @@ __device__ __forceinline__ void meta_unpack(const Grp<G, K> &g, const uint32_t (
     }
 }
 
-// Publish a frame (P, X, pivot|end, |R|, S) as it stands to the global ring
-// (one unit of global pending).  Warp-uniform call; true where it went.
+// Publish a frame (P, X, pivot|end, |R|, S, and R itself when listing) as it
+// stands to the global ring (one unit of global pending).  Warp-uniform call;
+// true where it went.
 template <int G, int K>
 __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchParams &prm, bool pred,
                                             const uint32_t (&P)[K], const uint32_t (&X)[K], unsigned pe, unsigned rs,
-                                            uint64_t S)
+                                            uint64_t S, bool list, const uint32_t (&R)[K])
 {
     constexpr int WP = G * K;
     const unsigned qmask = prm.qcap - 1u;
@@ -751,6 +755,7 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
         for (int k = 0; k < K; ++k) {
             __stcg(fr + kFrameHdr + g.gl * K + k, P[k]);
             __stcg(fr + kFrameHdr + WP + g.gl * K + k, X[k]);
+            if (list) __stcg(fr + kFrameHdr + 2 * WP + g.gl * K + k, R[k]);
         }
         if (g.leader()) {
             __stcg(fr + 0, pe);
@@ -774,7 +779,7 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
 // blocks outnumber its frames.  rows, hv, hist, lq are this block's staged
 // rows (or global rows), vertex hash terms, clique-size histogram and ring.
 // Called by all 32 lanes of every warp.
-template <int G, int K, bool SMEM, int PIVOT>
+template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint32_t *rows, const uint64_t *hv,
                                             const uint64_t *hk, uint32_t *hist, const LocalQ &lq, const Thresholds th,
                                             uint32_t *stack_smem, int stack_smem_levels, Counters &cn)
@@ -795,6 +800,12 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     bool lempty = true;  // the current frame's branching set is exhausted
     bool poller = false;
     unsigned gq = 0;  // global ring length last seen
+    // Clique listing (ListParams): this group's index, the |R| of the frame
+    // it took last, and (leader) the chunk it appends records to.
+    constexpr bool list = LIST;
+    const unsigned gidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32u / G) + g.lane / G;
+    unsigned rsb = 0, cpos = 0, cend = 0;
+    bool cfull = false;
 
     using Stk = Stack<G, K>;
     uint32_t stack_local[kStackDepth][Stk::LW];
@@ -808,15 +819,84 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     unsigned last_pend = 0xffffffffu, last_head = 0xffffffffu;
     unsigned backoff = 32;
     const unsigned qmask = prm.qcap - 1u;
-    const size_t lfs = frame_words(WP);
+    const size_t lfs = frame_words(WP, list);
 
     auto rowp = [&](int v) -> const uint32_t * { return rows + (size_t)v * WP + g.gl * K; };
+
+    // This lane's words of R for a frame of this group with |R| = r, plus
+    // vertex `extra` when it is >= 0 (listing only).
+    auto r_bits = [&](unsigned r, int extra, uint32_t (&out)[K]) {
+        const uint32_t *b = prm.lst.base + (size_t)gidx * WP + g.gl * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = b[k];
+        const uint16_t *pp = prm.lst.path + (size_t)gidx * n;
+        for (unsigned j = rsb; j < r; ++j) g.set(out, (int)pp[j]);
+        if (extra >= 0) g.set(out, extra);
+    };
+
+    // Append the maximal clique R u {v} (|R| = rs) as a record to this
+    // group's chunk.  Warp-uniform call; `emit` marks the groups reporting.
+    auto emit_clique = [&](bool emit, int v) {
+        const unsigned k = rs + 1u;
+        unsigned ok = 0u, wpos = 0u;
+        if (emit && g.leader()) {
+            const unsigned need = k + 1u, CW = prm.lst.chunk_words;
+            if (cpos + need > cend && !cfull) {
+                if (cend) prm.lst.fill[cend / CW - 1u] = cpos - (cend - CW);  // retire the chunk
+                const unsigned c = atomicAdd(prm.lst.next_chunk, 1u);
+                if (c < prm.lst.n_chunks) {
+                    cpos = c * CW;
+                    cend = cpos + CW;
+                } else {
+                    cpos = cend = 0u;
+                    cfull = true;
+                    atomicExch(prm.lst.overflow, 1u);
+                }
+            }
+            if (!cfull && cpos + need <= cend) {
+                ok = 1u;
+                wpos = cpos;
+                cpos += need;
+            }
+        }
+        ok = g.from_leader(ok);
+        wpos = g.from_leader(wpos);
+        uint32_t rb[K];
+        const uint32_t *b = prm.lst.base + (size_t)gidx * WP + g.gl * K;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) rb[kk] = (emit && ok) ? b[kk] : 0u;
+        int c = 0;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) c += __popc(rb[kk]);
+        int o = g.excl_scan(c);
+        if (emit && ok) {
+            // R of the taken frame fills slots [0, rsb), the path [rsb, rs),
+            // the leaf vertex slot rs
+            uint32_t *rec = prm.lst.rec + wpos + 1u;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                uint32_t w = rb[kk];
+                while (w) {
+                    if (o < (int)rsb) rec[o] = (g.gl * K + kk) * 32u + (unsigned)(__ffs(w) - 1);
+                    ++o;
+                    w &= w - 1u;
+                }
+            }
+            const uint16_t *pp = prm.lst.path + (size_t)gidx * n;
+            for (unsigned j = rsb + g.gl; j < rs; j += G) rec[j] = pp[j];
+            if (g.leader()) {
+                rec[rs] = (uint32_t)v;
+                prm.lst.rec[wpos] = 0x80000000u | k;
+            }
+        }
+    };
 
     // Take (P, X, pivot|end, |R|, S) as this group's frame.
     uint64_t t_busy = 0;
     auto start_frame = [&]() {
         work = true;
         lempty = false;
+        rsb = rs;
         if (g.leader()) t_busy = global_ns();
         d = dbase = 0;
         uint32_t rp[K];
@@ -859,13 +939,17 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 sL[k] = L[k];
             }
         }
+        uint32_t sR[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) sR[k] = 0u;
+        if (list && want) r_bits(srs, -1, sR);
         bool whole = false, gave;
         if (local)
-            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, (int)th.share_local, sP, sX, sL, spe, srs, sS, l1,
-                                            whole, cn.don);
+            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, (int)th.share_local, sP, sX, sL, spe, srs, sS,
+                                            list, sR, l1, whole, cn.don);
         else
             gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, (int)th.share_global, sP, sX, sL, spe, srs, sS,
-                                             l1, whole, cn.don);
+                                             list, sR, l1, whole, cn.don);
         if (gave) {
             if (from_stack) {
                 if (whole) {
@@ -961,6 +1045,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 for (int k = 0; k < K; ++k) {
                     P[k] = fr[kFrameHdr + g.gl * K + k];
                     X[k] = fr[kFrameHdr + WP + g.gl * K + k];
+                }
+                if (list) {
+                    uint32_t *b = prm.lst.base + (size_t)gidx * WP + g.gl * K;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) b[k] = fr[kFrameHdr + 2 * WP + g.gl * K + k];
                 }
             }
             __syncwarp();
@@ -1067,6 +1156,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     P[k] = __ldcg(fr + kFrameHdr + g.gl * K + k);
                     X[k] = __ldcg(fr + kFrameHdr + WP + g.gl * K + k);
                 }
+                if (list) {
+                    uint32_t *b = prm.lst.base + (size_t)gidx * WP + g.gl * K;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) b[k] = __ldcg(fr + kFrameHdr + 2 * WP + g.gl * K + k);
+                }
             }
             __syncwarp();
             if (got) {
@@ -1156,6 +1250,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 ++cn.intl;
             }
         }
+        if (list) {
+            const bool emit = act && !bp && !bx;
+            if (__ballot_sync(FULL, emit) != 0u) emit_clique(emit, v);
+        }
         const bool inter = act && bp;
 
         // ChoosePivotOrdered on the child (P', X')
@@ -1224,7 +1322,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             for (int k = 0; k < K; ++k) cp += __popc(Pc[k]);
             const int np = g.sum(cp);
             const bool sp = try_split && (unsigned)np >= th.split;
-            const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc);
+            uint32_t sR[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) sR[k] = 0u;
+            if (list && sp) r_bits(rs, v, sR);
+            const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc, list, sR);
             if (pushed) {
                 desc = false;
                 if (g.leader()) ++cn.don;
@@ -1242,7 +1344,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         if (__ballot_sync(FULL, spill) != 0u) {
             // stack full: the rest of this frame (L is non-empty) goes to the
             // global ring as it stands, and the group descends without it
-            const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S);
+            uint32_t sR[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) sR[k] = 0u;
+            if (list && spill) r_bits(rs, -1, sR);
+            const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S, list, sR);
             if (pushed && g.leader()) ++cn.don;
             if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
@@ -1254,15 +1360,17 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 X[k] = Xc[k];
                 L[k] = Lc[k];
             }
+            if (list) prm.lst.path[(size_t)gidx * n + rs] = (uint16_t)v;  // R grows by v at |R| = rs
             pe = (unsigned)pc | (n << 16);
             rs = rs + 1u;
             S = Sc;
         }
     }
-
+    if (list && g.leader() && cend)  // retire the last chunk
+        prm.lst.fill[cend / prm.lst.chunk_words - 1u] = cpos - (cend - prm.lst.chunk_words);
 }
 
-template <int G, int K, bool SMEM, int PIVOT>
+template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const SearchParams prm)
 {
     constexpr int WP = G * K;
@@ -1297,7 +1405,7 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
     uint32_t *stack_smem = reinterpret_cast<uint32_t *>(smem_raw + prm.stack_offset);
     Counters cn;
     if (ok)
-        search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : prm.rows, hv, hk, hist, lq, th, stack_smem,
+        search_loop<G, K, SMEM, PIVOT, LIST>(prm, SMEM ? srows : prm.rows, hv, hk, hist, lq, th, stack_smem,
                                        (int)prm.stack_smem_levels, cn);
     flush_counters(cn, prm.out);
     __syncthreads();
@@ -1424,11 +1532,12 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchP
         prm.trace = nullptr;
         prm.trace_per_block = 0;
         prm.tune = bp.tune;
+        prm.lst = ListParams{};
         const Thresholds th = density_thresholds(SMEM ? srows : gd.ren, n, WP, bp.tune.share_local,
                                                  bp.tune.share_global, bp.split_min_p, &root_key);
         Counters cn;
         if (ok)
-            search_loop<G, K, SMEM, PIVOT>(prm, SMEM ? srows : gd.ren, hv, hk, hist, lq, th,
+            search_loop<G, K, SMEM, PIVOT, false>(prm, SMEM ? srows : gd.ren, hv, hk, hist, lq, th,
                                            reinterpret_cast<uint32_t *>(smem_raw + bp.stack_offset),
                                            (int)bp.stack_smem_levels, cn);
         flush_counters(cn, gd.out);
@@ -1472,6 +1581,7 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
             else if (n > base) pw = (1u << (n - base)) - 1u;
             prm.frames[kFrameHdr + w] = pw;       // P = V
             prm.frames[kFrameHdr + WP + w] = 0u;  // X = {}
+            if (prm.lst.rec) prm.frames[kFrameHdr + 2 * WP + w] = 0u;  // R = {}
         }
     }
     if (tid == 0) {

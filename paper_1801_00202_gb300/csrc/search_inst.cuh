@@ -7,7 +7,7 @@
 
 namespace mce {
 
-template <int G, int K, bool SMEM, int PIVOT>
+template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStream_t s)
 {
     const unsigned *rp = nullptr;
@@ -19,21 +19,21 @@ cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStr
     search_init_kernel<G, K><<<64, 256, 0, s>>>(prm, rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sh.smem);
     if (e != cudaSuccess) return e;
-    search_kernel<G, K, SMEM, PIVOT><<<sh.blocks, sh.threads, sh.smem, s>>>(prm);
+    search_kernel<G, K, SMEM, PIVOT, LIST><<<sh.blocks, sh.threads, sh.smem, s>>>(prm);
     return cudaGetLastError();
 }
 
-template <int G, int K, bool SMEM, int PIVOT>
+template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT, LIST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<G, K, SMEM, PIVOT>, threads,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<G, K, SMEM, PIVOT, LIST>,
+                                                         threads, smem);
 }
 
 template <int G, int K, bool SMEM, int PIVOT>
@@ -53,36 +53,44 @@ cudaError_t batch_occupancy_t(int threads, size_t smem, int *blocks_per_sm)
                                                          smem);
 }
 
-template <int G, int K, bool SMEM, int PIVOT>
+// The listing variant (LIST) has no batched form.
+template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 SearchImpl impl_t()
 {
-    return {run_search_t<G, K, SMEM, PIVOT>, occupancy_t<G, K, SMEM, PIVOT>, run_batch_t<G, K, SMEM, PIVOT>,
-            batch_occupancy_t<G, K, SMEM, PIVOT>};
+    if constexpr (LIST)
+        return {run_search_t<G, K, SMEM, PIVOT, true>, occupancy_t<G, K, SMEM, PIVOT, true>, nullptr, nullptr};
+    else
+        return {run_search_t<G, K, SMEM, PIVOT, false>, occupancy_t<G, K, SMEM, PIVOT, false>,
+                run_batch_t<G, K, SMEM, PIVOT>, batch_occupancy_t<G, K, SMEM, PIVOT>};
 }
 
-template <int G, int K, bool SMEM>
+template <int G, int K, bool SMEM, bool LIST>
 SearchImpl pick_pivot(int pivot)
 {
     switch (pivot) {
-    case MCE_PIVOT_GREEDY: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY>();
-    case MCE_PIVOT_GREEDY_TX: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX>();
-    case MCE_PIVOT_TOMITA: return impl_t<G, K, SMEM, MCE_PIVOT_TOMITA>();
+    case MCE_PIVOT_GREEDY: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY, LIST>();
+    case MCE_PIVOT_GREEDY_TX: return impl_t<G, K, SMEM, MCE_PIVOT_GREEDY_TX, LIST>();
+    case MCE_PIVOT_TOMITA: return impl_t<G, K, SMEM, MCE_PIVOT_TOMITA, LIST>();
     default: return {nullptr, nullptr, nullptr, nullptr};
     }
 }
 
 // Rows live in shared memory only for sets of at most 32 words.
-template <int G, int K>
+template <int G, int K, bool LIST>
 SearchImpl pick(bool smem, int pivot)
 {
     if constexpr (G * K <= 32) {
-        if (smem) return pick_pivot<G, K, true>(pivot);
+        if (smem) return pick_pivot<G, K, true, LIST>(pivot);
     }
     if (smem) return {nullptr, nullptr, nullptr, nullptr};
-    return pick_pivot<G, K, false>(pivot);
+    return pick_pivot<G, K, false, LIST>(pivot);
 }
 
 }  // namespace mce
 
 #define MCE_DEFINE_SEARCH(G, K) \
-    namespace mce { SearchImpl search_impl_##G##_##K(bool smem, int pivot) { return pick<G, K>(smem, pivot); } }
+    namespace mce { SearchImpl search_impl_##G##_##K(bool smem, int pivot) { return pick<G, K, false>(smem, pivot); } }
+#define MCE_DEFINE_SEARCH_LIST(G, K)                                        \
+    namespace mce {                                                         \
+    SearchImpl search_list_impl_##G##_##K(bool smem, int pivot) { return pick<G, K, true>(smem, pivot); } \
+    }

@@ -1,0 +1,3 @@
+// Listing variants of the search kernels with 2 lanes per subtree and 4 words per lane.
+#include "search_inst.cuh"
+MCE_DEFINE_SEARCH_LIST(2, 4)

@@ -1,0 +1,3 @@
+// Listing variants of the search kernels with 32 lanes per subtree and 1 word per lane.
+#include "search_inst.cuh"
+MCE_DEFINE_SEARCH_LIST(32, 1)
