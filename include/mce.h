@@ -303,7 +303,12 @@ int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
                         const mce_options *opts, mce_result *res);
 
 /* Served form: requests are admitted by device memory and run with the
- * others already on the GPU; mce_poll never blocks. */
+ * others already on the GPU; mce_poll never blocks.  Each admitted request
+ * runs its whole path on one of 128 streams with a grid sized by its expected
+ * cost; requests overlap on the device only as far as CUDA maps their streams
+ * to separate hardware queues, so set CUDA_DEVICE_MAX_CONNECTIONS=32 in the
+ * environment before the process creates its CUDA context (the Python
+ * binding does this when imported first). */
 int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out);
 int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res);
 int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res);

@@ -15,6 +15,12 @@ import os
 
 import numpy as np
 
+# The served form runs every admitted request on its own stream; CUDA maps
+# streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless set), and
+# streams sharing a queue run one after another.  Ask for the most queues
+# unless the caller chose; it takes effect only if no CUDA context exists yet.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 from .build import LIB as _LIB_PATH, build  # noqa: F401
 
 MCE_OK, MCE_PENDING = 0, 1

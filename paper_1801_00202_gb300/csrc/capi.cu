@@ -133,7 +133,9 @@ unsigned default_threads(uint32_t n, int K)
     return K >= 4 ? 512u : 1024u;
 }
 
-int choose(uint32_t n, const mce_options &o, Config &c)
+// stack_cap: most shared memory for the explicit stack per block (the served
+// form keeps blocks small so that several requests share an SM).
+int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(size_t)0)
 {
     if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
         return MCE_EINVAL;
@@ -161,8 +163,9 @@ int choose(uint32_t n, const mce_options &o, Config &c)
 
     c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n, K);
     if (c.threads % 32 || c.threads > (K >= 4 ? 512u : 1024u)) return MCE_EINVAL;
-    plan_stack_for((uint32_t)search_smem(n, c.wp, c.smem, c.list), c.G, c.K, c.threads, limit, c.stack_levels,
-                   c.stack_offset, c.smem_bytes);
+    const size_t base = search_smem(n, c.wp, c.smem, c.list);
+    const size_t cap = stack_cap < limit - base ? base + stack_cap : limit;
+    plan_stack_for((uint32_t)base, c.G, c.K, c.threads, cap, c.stack_levels, c.stack_offset, c.smem_bytes);
     if (o.blocks) {
         c.blocks = o.blocks;
     } else {
@@ -203,7 +206,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 4u, 16u, 2000u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 4u, 16u, 2000u, 50000u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -216,6 +219,7 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "local_check") && val) d.local_check = val;
                 else if (!std::strcmp(key, "global_check") && val) d.global_check = val;
                 else if (!std::strcmp(key, "refresh_ns")) d.refresh_ns = val;
+                else if (!std::strcmp(key, "serve_cpb") && val) d.serve_cpb = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -1146,13 +1150,15 @@ extern "C" int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint3
 
 namespace {
 
-constexpr int kServeSlots = 48;
-constexpr double kCliquesPerBlock = 20000.0;
+constexpr int kServeSlots = 128;
+constexpr size_t kServeStackBytes = 56 * 1024;  // shared-memory stack per block
 
 struct Request {
     mce_ticket id = 0;
     mce_graph *g = nullptr;
     mce_options o{};
+    Config c;
+    Layout L;
     uint64_t scratch_bytes = 0, out_bytes = 0, need = 0;
     void *scratch = nullptr;
     uint64_t *d_out = nullptr;
@@ -1224,7 +1230,8 @@ bool admit(Server *sv, Request *r)
     sv->in_use += r->need;
     cudaError_t e = cudaEventRecord(sv->ev0[slot], s);
     if (e == cudaSuccess) {
-        rc = mce_enumerate_device(r->g->n, r->g->w, r->g->d_rows, &r->o, r->scratch, r->scratch_bytes, r->d_out, s);
+        rc = enumerate_device_impl(r->g->n, r->g->w, r->g->d_rows, r->o, r->c, r->L,
+                                   static_cast<unsigned char *>(r->scratch), r->d_out, s, nullptr);
         if (rc == MCE_OK)
             e = cudaMemcpyAsync(sv->pinned[slot], r->d_out, r->out_bytes, cudaMemcpyDeviceToHost, s);
         if (rc == MCE_OK && e == cudaSuccess) e = cudaEventRecord(sv->ev1[slot], s);
@@ -1350,14 +1357,17 @@ extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, m
     if (!o.threads_per_block) o.threads_per_block = 256;
     if (!o.blocks) {
         const double cost = expected_cliques(g->n, g->m);
-        o.blocks = (uint32_t)std::min<double>(std::max(1.0, std::ceil(cost / kCliquesPerBlock)), 4.0 * sv->sms);
+        const double per_block = default_tuning().serve_cpb;
+        o.blocks = (uint32_t)std::min<double>(std::max(1.0, std::ceil(cost / per_block)), 4.0 * sv->sms);
     }
     Request *r = new (std::nothrow) Request;
     if (!r) return MCE_ENOMEM;
     r->g = g;
     r->o = o;
-    int rc = mce_scratch_bytes(g->n, &o, &r->scratch_bytes);
+    int rc = g->n > MCE_NMAX ? MCE_EINVAL : choose(g->n, o, r->c, kServeStackBytes);
     if (rc) { delete r; return rc; }
+    r->L = layout(g->n, r->c);
+    r->scratch_bytes = r->L.total;
     r->out_bytes = MCE_OUT_WORDS(g->n) * 8;
     r->need = r->scratch_bytes + r->out_bytes;
     r->t_submit = std::chrono::steady_clock::now();

@@ -82,6 +82,7 @@ struct Tuning {
     uint32_t local_check;   // busy warps: iterations between block-ring checks
     uint32_t global_check;  // busy warps: iterations between global checks
     uint32_t refresh_ns;    // age of a block's cached view of the global ring
+    uint32_t serve_cpb;     // served form: expected maximal cliques per block
 };
 
 struct SearchParams {
@@ -216,6 +217,12 @@ cudaError_t launch_renumber_batch(const BatchGraph *graphs, uint32_t count, uint
                                   cudaStream_t s);
 
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Raise a kernel's dynamic shared-memory limit to the device maximum and
+// prefer the largest shared-memory carveout, once per (kernel, device).  Every
+// launch after that runs under the same settings, so kernels of different
+// requests on different streams never wait for one another to change them.
+cudaError_t kernel_smem_setup(const void *func);
 
 // Listing post-pass (listing.cu): record chunks of a finished listing search
 // -> CSR listing (off[count + 1], ids) in original labels, each clique in

@@ -5,6 +5,9 @@
 //  * renumbering by position (Section 4.2, "How we use the vertex ordering").
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "mce_internal.h"
@@ -222,15 +225,15 @@ cudaError_t launch_order(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t 
     const uint32_t words = (n + 31) / 32;  // words that can hold set bits
     cudaError_t e;
     if (words <= 32) {
-        e = cudaFuncSetAttribute(order_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = kernel_smem_setup((const void *)order_kernel<1>);
         if (e != cudaSuccess) return e;
         order_kernel<1><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
     } else if (words <= 64) {
-        e = cudaFuncSetAttribute(order_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = kernel_smem_setup((const void *)order_kernel<2>);
         if (e != cudaSuccess) return e;
         order_kernel<2><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
     } else {
-        e = cudaFuncSetAttribute(order_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = kernel_smem_setup((const void *)order_kernel<4>);
         if (e != cudaSuccess) return e;
         order_kernel<4><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
     }
@@ -253,6 +256,29 @@ cudaError_t launch_renumber(uint32_t n, uint32_t w, const uint32_t *rows, const 
     return cudaGetLastError();
 }
 
+
+cudaError_t kernel_smem_setup(const void *func)
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+        if (d.first == func && d.second == dev) return cudaSuccess;
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e == cudaSuccess)  // static shared memory counts against the same limit
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && (int)done.size() < kMaxDev * 256) done.emplace_back(func, dev);
+    return e;
+}
 
 cudaError_t prepare_order_batch(uint32_t max_n, uint32_t max_w, size_t *smem)
 {

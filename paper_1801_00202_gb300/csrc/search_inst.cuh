@@ -19,8 +19,7 @@ cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStr
     search_init_kernel<G, K><<<64, 256, 0, s>>>(prm, rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sh.smem);
+    e = kernel_smem_setup((const void *)search_kernel<G, K, SMEM, PIVOT, LIST>);
     if (e != cudaSuccess) return e;
     search_kernel<G, K, SMEM, PIVOT, LIST><<<sh.blocks, sh.threads, sh.smem, s>>>(prm);
     return cudaGetLastError();
@@ -29,8 +28,7 @@ cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStr
 template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<G, K, SMEM, PIVOT, LIST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = kernel_smem_setup((const void *)search_kernel<G, K, SMEM, PIVOT, LIST>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<G, K, SMEM, PIVOT, LIST>,
                                                          threads, smem);
