@@ -138,6 +138,9 @@ typedef struct {
 #define MCE_OUT_BUSY_NS   10   /* subtree-group time spent holding a frame:
                                   utilisation = busy / (groups x duration)   */
 #define MCE_OUT_GROUPS    11   /* subtree groups of the launch               */
+#define MCE_OUT_GPUSH     12   /* frames published to the device-wide queue  */
+#define MCE_OUT_GTRY      13   /* attempts to take a frame from it           */
+#define MCE_OUT_CAS_FAIL  14   /* lost compare-and-swap races on its tickets */
 #define MCE_OUT_HIST       16
 #define MCE_OUT_WORDS(n)   (MCE_OUT_HIST + (uint64_t)(n) + 1)
 

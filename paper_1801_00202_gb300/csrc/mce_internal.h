@@ -83,6 +83,7 @@ struct Tuning {
     uint32_t global_check;  // busy warps: iterations between global checks
     uint32_t refresh_ns;    // age of a block's cached view of the global ring
     uint32_t serve_cpb;     // served form: expected maximal cliques per block
+    uint32_t pop_tries;     // ticket attempts of one take from the device-wide ring
 };
 
 struct SearchParams {

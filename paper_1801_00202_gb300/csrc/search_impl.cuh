@@ -150,7 +150,8 @@ __device__ __forceinline__ void set_status(uint64_t *out, Ctl *ctl, int code)
 // seq == ticket is free for producer `ticket`, seq == ticket + 1 holds the
 // frame for consumer `ticket`).
 
-__device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket)
+__device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
+                                               uint64_t &fails)
 {
     unsigned pos = ld_relaxed(&ctl->tail);
     for (unsigned t = 0; t < kCasTries; ++t) {
@@ -159,6 +160,7 @@ __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned
         if (dif == 0) {
             unsigned prev = atomicCAS(&ctl->tail, pos, pos + 1);
             if (prev == pos) { ticket = pos; return true; }
+            ++fails;
             pos = prev;
         } else if (dif < 0) {
             return false;  // full
@@ -169,15 +171,17 @@ __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned
     return false;
 }
 
-__device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket)
+__device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
+                                              uint64_t &fails, unsigned tries = kCasTries)
 {
     unsigned pos = ld_relaxed(&ctl->head);
-    for (unsigned t = 0; t < kCasTries; ++t) {
+    for (unsigned t = 0; t < tries; ++t) {
         unsigned s = ld_acquire(&seq[pos & mask]);
         int dif = (int)(s - (pos + 1));
         if (dif == 0) {
             unsigned prev = atomicCAS(&ctl->head, pos, pos + 1);
             if (prev == pos) { ticket = pos; return true; }
+            ++fails;
             pos = prev;
         } else if (dif < 0) {
             return false;  // empty
@@ -405,6 +409,13 @@ __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned grou
     }
 }
 
+// Per-warp result counters (meaningful in group leaders; summed at the end).
+struct Counters {
+    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0, gsteals = 0, busy = 0;
+    uint64_t gpush = 0, gtry = 0, cas_fail = 0;  // device-wide ring diagnostics
+    unsigned max = 0;
+};
+
 // ---------------------------------------------------------------------------
 // Give away the front of a frame's branching set L (c elements, in order).
 // The taker gets L1 = the first `give` elements as the frame
@@ -422,7 +433,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
                                              bool pred, bool allow_whole, int min_p, const uint32_t (&P)[K],
                                              const uint32_t (&X)[K], const uint32_t (&L)[K], unsigned pe,
                                              unsigned rs, uint64_t S, bool list, const uint32_t (&R)[K],
-                                             uint32_t (&l1)[K], bool &whole, uint64_t &c_don)
+                                             uint32_t (&l1)[K], bool &whole, Counters &cn)
 {
     constexpr int WP = G * K;
     int cl = 0, cp = 0;
@@ -472,7 +483,8 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
             if (!got) atomicSub(&lq.h->bwork, 1u);
         } else {
             atomicAdd(&prm.ctl->pending, 1u);
-            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket) ? 1u : 0u;
+            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket, cn.cas_fail) ? 1u : 0u;
+            cn.gpush += got;
             if (!got) atomicSub(&prm.ctl->pending, 1u);
         }
     }
@@ -522,17 +534,11 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
         } else {
             st_release(&prm.seq[ticket & (prm.qcap - 1u)], ticket + 1u);
         }
-        ++c_don;
+        ++cn.don;
     }
     whole = give >= c;
     return got != 0u;
 }
-
-// Per-warp result counters (meaningful in group leaders; summed at the end).
-struct Counters {
-    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0, gsteals = 0, busy = 0;
-    unsigned max = 0;
-};
 
 // Warp-reduce the counters and add them to out[] (one atomic per counter per
 // warp).  Called by all 32 lanes.
@@ -549,6 +555,9 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         c.steals += __shfl_xor_sync(FULL, c.steals, o);
         c.gsteals += __shfl_xor_sync(FULL, c.gsteals, o);
         c.busy += __shfl_xor_sync(FULL, c.busy, o);
+        c.gpush += __shfl_xor_sync(FULL, c.gpush, o);
+        c.gtry += __shfl_xor_sync(FULL, c.gtry, o);
+        c.cas_fail += __shfl_xor_sync(FULL, c.cas_fail, o);
         c.max = max(c.max, __shfl_xor_sync(FULL, c.max, o));
     }
     if ((threadIdx.x & 31u) == 0) {
@@ -562,6 +571,9 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         if (c.steals) atomicAdd(o + MCE_OUT_STEALS, c.steals);
         if (c.gsteals) atomicAdd(o + MCE_OUT_GLOBAL, c.gsteals);
         if (c.busy) atomicAdd(o + MCE_OUT_BUSY_NS, c.busy);
+        if (c.gpush) atomicAdd(o + MCE_OUT_GPUSH, c.gpush);
+        if (c.gtry) atomicAdd(o + MCE_OUT_GTRY, c.gtry);
+        if (c.cas_fail) atomicAdd(o + MCE_OUT_CAS_FAIL, c.cas_fail);
         if (c.max) atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)c.max);
     }
 }
@@ -737,14 +749,15 @@ __device__ __forceinline__ void meta_unpack(const Grp<G, K> &g, const uint32_t (
 template <int G, int K>
 __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchParams &prm, bool pred,
                                             const uint32_t (&P)[K], const uint32_t (&X)[K], unsigned pe, unsigned rs,
-                                            uint64_t S, bool list, const uint32_t (&R)[K])
+                                            uint64_t S, bool list, const uint32_t (&R)[K], Counters &cn)
 {
     constexpr int WP = G * K;
     const unsigned qmask = prm.qcap - 1u;
     unsigned ticket = 0, got = 0;
     if (pred && g.leader()) {
         atomicAdd(&prm.ctl->pending, 1u);
-        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket) ? 1u : 0u;
+        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket, cn.cas_fail) ? 1u : 0u;
+        cn.gpush += got;
         if (!got) atomicSub(&prm.ctl->pending, 1u);
     }
     got = g.from_leader(got);
@@ -946,10 +959,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         bool whole = false, gave;
         if (local)
             gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, (int)th.share_local, sP, sX, sL, spe, srs, sS,
-                                            list, sR, l1, whole, cn.don);
+                                            list, sR, l1, whole, cn);
         else
             gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, (int)th.share_global, sP, sX, sL, spe, srs, sS,
-                                             list, sR, l1, whole, cn.don);
+                                             list, sR, l1, whole, cn);
         if (gave) {
             if (from_stack) {
                 if (whole) {
@@ -1139,10 +1152,18 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             const unsigned queued = tail - head;
             gq = queued;
 
-            // idle groups take a global frame when their block's ring is empty
+            // An idle group takes a global frame when its block's ring is
+            // empty; only the block's polling warp asks, one group per try, so
+            // the ring's head sees one contender per block instead of one per
+            // idle group (the block's other groups get work from the taker
+            // through the block ring).
             unsigned ticket = 0, got = 0;
-            if (!work && queued != 0u && lt == lh && g.leader())
-                got = q_reserve_pop(ctl, prm.seq, qmask, ticket) ? 1u : 0u;
+            const bool ask = !work && queued != 0u && lt == lh && poller && g.leader();
+            const unsigned askers = __ballot_sync(FULL, ask);
+            if (ask && g.lane == (unsigned)(__ffs(askers) - 1)) {
+                ++cn.gtry;
+                got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.cas_fail, prm.tune.pop_tries) ? 1u : 0u;
+            }
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
             if (got) {
@@ -1326,7 +1347,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 #pragma unroll
             for (int k = 0; k < K; ++k) sR[k] = 0u;
             if (list && sp) r_bits(rs, v, sR);
-            const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc, list, sR);
+            const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc, list, sR, cn);
             if (pushed) {
                 desc = false;
                 if (g.leader()) ++cn.don;
@@ -1348,7 +1369,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 #pragma unroll
             for (int k = 0; k < K; ++k) sR[k] = 0u;
             if (list && spill) r_bits(rs, -1, sR);
-            const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S, list, sR);
+            const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S, list, sR, cn);
             if (pushed && g.leader()) ++cn.don;
             if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
