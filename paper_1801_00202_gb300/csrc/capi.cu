@@ -206,7 +206,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 4u, 16u, 2000u, 50000u, 16384u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 4u, 16u, 2000u, 50000u, 16384u, 32u, 16384u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -221,6 +221,8 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "refresh_ns")) d.refresh_ns = val;
                 else if (!std::strcmp(key, "serve_cpb") && val) d.serve_cpb = val;
                 else if (!std::strcmp(key, "pop_tries") && val) d.pop_tries = val;
+                else if (!std::strcmp(key, "share_tail") && val) d.share_tail = val;
+                else if (!std::strcmp(key, "idle_sleep_ns") && val) d.idle_sleep_ns = val;
                 p += used;
                 if (*p == ',') ++p;
             }

@@ -84,6 +84,8 @@ struct Tuning {
     uint32_t refresh_ns;    // age of a block's cached view of the global ring
     uint32_t serve_cpb;     // served form: expected maximal cliques per block
     uint32_t pop_tries;     // ticket attempts of one take from the device-wide ring
+    uint32_t share_tail;    // smallest |P| shared once half the groups/blocks are idle
+    uint32_t idle_sleep_ns; // longest back-off of an idle warp that is not polling
 };
 
 struct SearchParams {

@@ -920,7 +920,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 
     // Share the shallowest frame this group owns (the stack bottom, else the
     // current frame) through level LOCAL (true: block ring, false: global).
-    auto share = [&](bool want, bool local) {
+    auto share = [&](bool want, bool local, int min_p) {
         const bool from_stack = want && d > dbase;
         uint32_t sP[K], sX[K], sL[K], l1[K];
         uint32_t mr[Stk::M];
@@ -958,10 +958,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         if (list && want) r_bits(srs, -1, sR);
         bool whole = false, gave;
         if (local)
-            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, (int)th.share_local, sP, sX, sL, spe, srs, sS,
+            gave = donate_front<G, K, true>(g, prm, lq, want, from_stack, min_p, sP, sX, sL, spe, srs, sS,
                                             list, sR, l1, whole, cn);
         else
-            gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, (int)th.share_global, sP, sX, sL, spe, srs, sS,
+            gave = donate_front<G, K, false>(g, prm, lq, want, from_stack, min_p, sP, sX, sL, spe, srs, sS,
                                              list, sR, l1, whole, cn);
         if (gave) {
             if (from_stack) {
@@ -1076,7 +1076,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 start_frame();
             }
             const bool hungry = work && !got && li > lqueued;
-            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, true);
+            // with half the block's groups idle, smaller frames are worth moving
+            const unsigned bgroups = (blockDim.x >> 5) * (32u / G);
+            const int lmin = 2u * li > bgroups ? (int)min(th.share_local, prm.tune.share_tail) : (int)th.share_local;
+            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, true, lmin);
         }
 
         // ---- B2: the global ring and the end of the search.  Global state is
@@ -1157,10 +1160,13 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             // the ring's head sees one contender per block instead of one per
             // idle group (the block's other groups get work from the taker
             // through the block ring).
+            // (A block-private ring, as in the batched form, has no other
+            // contenders: there every idle group asks.)
             unsigned ticket = 0, got = 0;
-            const bool ask = !work && queued != 0u && lt == lh && poller && g.leader();
+            const bool ring_shared = prm.total_groups > (blockDim.x >> 5) * (32u / G);
+            const bool ask = !work && queued != 0u && lt == lh && (poller || !ring_shared) && g.leader();
             const unsigned askers = __ballot_sync(FULL, ask);
-            if (ask && g.lane == (unsigned)(__ffs(askers) - 1)) {
+            if (ask && (!ring_shared || g.lane == (unsigned)(__ffs(askers) - 1))) {
                 ++cn.gtry;
                 got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.cas_fail, prm.tune.pop_tries) ? 1u : 0u;
             }
@@ -1203,7 +1209,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 
             // busy groups feed starving blocks
             const bool hungry = work && !got && starving > queued;
-            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, false);
+            // with half the blocks starving (the search is draining), so are
+            // smaller frames
+            const int gmin = 2u * starving > gridDim.x ? (int)min(th.share_global, prm.tune.share_tail)
+                                                       : (int)th.share_global;
+            if (__ballot_sync(FULL, hungry) != 0u) share(hungry, false, gmin);
 
             if (__ballot_sync(FULL, work) == 0u) {
                 // nobody here has work: back off; the poller watches for a
@@ -1218,8 +1228,12 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                         set_status(prm.out, ctl, MCE_ETIMEOUT);
                     }
                 }
+                // the poller backs off to 1 us; other idle warps only wait for
+                // the block ring and may sleep longer (fewer issue slots taken
+                // from the busy warps of the SM)
                 __nanosleep(backoff);
-                backoff = backoff < 1024u ? backoff * 2u : 1024u;
+                const unsigned cap = poller ? 1024u : prm.tune.idle_sleep_ns;
+                backoff = backoff < cap ? backoff * 2u : cap;
                 continue;
             }
             backoff = 32;
