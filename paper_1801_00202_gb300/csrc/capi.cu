@@ -206,7 +206,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 4u, 16u, 2000u, 50000u, 16384u, 32u, 16384u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
