@@ -234,23 +234,33 @@ def plain_pass(mce, torch, graphs, opts):
 def batched_form(mce, torch, ctx, s, specs, opts, args, flush_l2):
     graphs = [ctx.load_bitset(n, rows) for n, _, _, rows in specs]
     ns = [n for n, _, _, _ in specs]
-    t = time.perf_counter()
-    b = mce.Batch(ctx, graphs, opts)
-    plan_s = time.perf_counter() - t
-    for _ in range(max(1, args.warmup // 3)):
-        b.run()
     mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    evs = [(mk(), mk()) for _ in range(args.batch_steps)]
-    torch.cuda.synchronize()
-    for e0, e1 in evs:
-        flush_l2()
-        e0.record(s)
-        b.launch()
-        e1.record(s)
-    res = b.results()
-    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    plain, plain_s = plain_pass(mce, torch, graphs, opts)
+
+    def timed(b):
+        for _ in range(max(1, args.warmup // 3)):
+            b.run()
+        evs = [(mk(), mk()) for _ in range(args.batch_steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush_l2()
+            e0.record(s)
+            b.launch()
+            e1.record(s)
+        res = b.results()
+        return res, [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    # the launch choices come from the autotuner (timed on these graphs at
+    # plan time, outside the timed region); the defaults are measured beside
+    t = time.perf_counter()
+    b = mce.Batch(ctx, graphs, mce.options(autotune=True))
+    plan_s = time.perf_counter() - t
+    res, ms = timed(b)
+    buckets = b.buckets()
     b.close()
+    b = mce.Batch(ctx, graphs, opts)
+    res_d, ms_d = timed(b)
+    b.close()
+    plain, plain_s = plain_pass(mce, torch, graphs, opts)
     for g in graphs:
         g.free()
     sec = statistics.mean(ms) / 1e3
@@ -260,12 +270,16 @@ def batched_form(mce, torch, ctx, s, specs, opts, args, flush_l2):
                        f"(n,p) redrawn while E[maximal cliques] > 1e6",
            "graphs": len(ns), "acceptance": len(ns) / sum(d for _, _, d, _ in specs),
            "mean_n": float(np.mean(ns)), "cliques": cliques, "nodes": nodes,
-           "steps": args.batch_steps, "ms_per_step": statistics.mean(ms), "plan_and_capture_s": plan_s,
+           "steps": args.batch_steps, "ms_per_step": statistics.mean(ms), "autotune_plan_and_capture_s": plan_s,
            "batched": _rates(len(ns), cliques, nodes, ops, rb, sec),
+           "batched_default_choices": _rates(len(ns), cliques, nodes, ops, rb, statistics.mean(ms_d) / 1e3),
+           "autotuned_buckets": [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in x.items()}
+                                 for x in buckets],
            "plain": _rates(len(ns), cliques, nodes, ops, rb, plain_s),
            "plain_note": "one mce_enumerate per graph, back to back (wall clock, results read per graph)",
            "status_ok": all(r["status"] == 0 for r in res),
-           "batched_equals_plain": all(_same(a, c) for a, c in zip(res, plain)),
+           "batched_equals_plain": all(_same(a, c) for a, c in zip(res, plain)) and
+                                   all(_same(a, c) for a, c in zip(res_d, plain)),
            "launches_per_step": "one CUDA graph: a batched ordering kernel, a batched renumbering "
                                 "kernel and one persistent search kernel per subtree shape"}
     out["speedup_graphs_per_s"] = out["batched"]["graphs_per_s"] / out["plain"]["graphs_per_s"]

@@ -89,6 +89,10 @@ extern "C" {
                                       served requests: MCE_ENOTIMPL); each
                                       clique's labels ascending, cliques in
                                       no particular order                   */
+#define MCE_AUTOTUNE         0x8u  /* batched form: measure the launch choice
+                                      of every words-per-row class on the
+                                      batch's own graphs (see
+                                      mce_batch_create)                      */
 #define MCE_LIST_SORTED      0x4u  /* MCE_LIST with the cliques in
                                       lexicographic order (the problem's
                                       output, Section 2: all maximal cliques) */
@@ -295,6 +299,31 @@ int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
 typedef struct mce_batch mce_batch;
 int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
                      const mce_options *opts, mce_batch **out);
+
+/* Autotuning (MCE_AUTOTUNE in opts->flags, with lanes_per_subtree,
+ * words_per_lane, threads_per_block and split_min_p left 0): graphs are
+ * classed by words per row (1, 2, 4, ..., 128).  Classes with a choice cached
+ * in the context (per class and pivot rule) take it; the others, if they hold
+ * at least 16 graphs of the batch, are tuned by coordinate descent in
+ * decreasing order of expected work: every candidate for the class -- 1, 2
+ * or 4 words per lane with the fewest lanes that hold a row, 128 / 256 / 512
+ * threads per block, then the best with the breadth-first split off -- is
+ * timed as one captured launch of the whole batch (up to 4096 of its graphs,
+ * sampled evenly) with the other classes at their current choice, and the
+ * fastest is kept and cached.  Classes with fewer graphs use the built-in
+ * defaults.  Tuning runs inside mce_batch_create (seconds for thousands of
+ * graphs); mce_batch_launch replays the chosen plan. */
+typedef struct {
+    uint32_t words_class;        /* rows of at most this many 32-bit words  */
+    uint32_t graphs;             /* graphs of the batch in this bucket      */
+    uint32_t lanes_per_subtree, words_per_lane, threads_per_block, blocks;
+    uint32_t split_min_p;        /* 0 = by density, 0xffffffff = never      */
+    uint32_t tuned;              /* 1 when the choice was measured          */
+    double tuned_ms_per_graph;   /* best measured time per graph (tuning)   */
+} mce_batch_bucket;
+/* The launch choice of every bucket of a batch: up to cap entries to out,
+ * the number of buckets to *count. */
+int mce_batch_buckets(const mce_batch *b, mce_batch_bucket *out, uint32_t cap, uint32_t *count);
 int mce_batch_launch(mce_batch *b);
 int mce_batch_results(mce_batch *b, mce_result *res);
 int mce_batch_run(mce_batch *b, mce_result *res);

@@ -30,7 +30,7 @@ MCE_NMAX = 4096
 
 MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA = 0, 1, 2
 PIVOTS = {"greedy": 0, "tx": 1, "tomita": 2}
-MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED = 0x1, 0x2, 0x4
+MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED, MCE_AUTOTUNE = 0x1, 0x2, 0x4, 0x8
 
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
 MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
@@ -56,6 +56,12 @@ class Options(C.Structure):
                 ("split_min_p", C.c_uint32), ("_reserved", C.c_uint32)]
 
 
+class BatchBucket(C.Structure):
+    _fields_ = [("words_class", C.c_uint32), ("graphs", C.c_uint32), ("lanes_per_subtree", C.c_uint32),
+                ("words_per_lane", C.c_uint32), ("threads_per_block", C.c_uint32), ("blocks", C.c_uint32),
+                ("split_min_p", C.c_uint32), ("tuned", C.c_uint32), ("tuned_ms_per_graph", C.c_double)]
+
+
 class Result(C.Structure):
     _fields_ = [("count", C.c_uint64), ("nodes", C.c_uint64), ("internal_nodes", C.c_uint64),
                 ("dead_ends", C.c_uint64), ("hash", C.c_uint64), ("max_size", C.c_uint32),
@@ -67,10 +73,10 @@ class Result(C.Structure):
 
 def options(pivot: str | int = "greedy", identity_order: bool = False, lanes: int = 0, words: int = 0,
             blocks: int = 0, threads: int = 0, timeout_ns: int = 0, stack_levels: int = 0,
-            queue_log2: int = 0, split_min_p: int = 0, flags: int = 0) -> Options:
+            queue_log2: int = 0, split_min_p: int = 0, flags: int = 0, autotune: bool = False) -> Options:
     o = Options()
     o.pivot_mode = PIVOTS[pivot] if isinstance(pivot, str) else int(pivot)
-    o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0)
+    o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0) | (MCE_AUTOTUNE if autotune else 0)
     o.lanes_per_subtree, o.words_per_lane = lanes, words
     o.blocks, o.threads_per_block = blocks, threads
     o.timeout_ns, o.stack_levels, o.queue_log2 = timeout_ns, stack_levels, queue_log2
@@ -103,6 +109,7 @@ _SIGS = {
     "mce_batch_results": (C.c_int, [_VP, C.POINTER(Result)]),
     "mce_batch_run": (C.c_int, [_VP, C.POINTER(Result)]),
     "mce_batch_destroy": (None, [_VP]),
+    "mce_batch_buckets": (C.c_int, [_VP, C.POINTER(BatchBucket), _U32, C.POINTER(_U32)]),
     "mce_submit": (C.c_int, [_VP, _VP, C.POINTER(Options), C.POINTER(_U64)]),
     "mce_poll": (C.c_int, [_VP, _U64, C.POINTER(Result)]),
     "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
@@ -403,6 +410,14 @@ class Batch:
 
     def launch(self):
         _check(lib().mce_batch_launch(self.handle), "mce_batch_launch")
+
+    def buckets(self) -> list:
+        """mce_batch_buckets: the launch choice of every bucket."""
+        n = C.c_uint32(0)
+        _check(lib().mce_batch_buckets(self.handle, None, 0, C.byref(n)), "mce_batch_buckets")
+        arr = (BatchBucket * max(n.value, 1))()
+        _check(lib().mce_batch_buckets(self.handle, arr, n.value, C.byref(n)), "mce_batch_buckets")
+        return [{f: getattr(arr[i], f) for f, _ in BatchBucket._fields_} for i in range(n.value)]
 
     def results(self, raise_on_error: bool = True):
         rc = lib().mce_batch_results(self.handle, self._res)

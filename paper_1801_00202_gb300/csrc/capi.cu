@@ -6,6 +6,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -394,6 +395,15 @@ extern "C" int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const ui
 
 struct Server;
 
+// A batch bucket's launch choice: subtree shape, block size, split threshold.
+struct TuneChoice {
+    int G = 0, K = 0;
+    unsigned threads = 0;
+    uint32_t split = 0;
+    bool tuned = false;
+    double ms_per_graph = 0.0;
+};
+
 struct mce_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -402,6 +412,8 @@ struct mce_ctx {
     uint64_t budget = 0;
     std::atomic<uint64_t> used{0};
     Server *server = nullptr;  // started by the first mce_submit
+    std::mutex tune_mu;        // autotuned batch choices by (words class, pivot)
+    std::map<uint32_t, TuneChoice> tuned;
 };
 
 struct mce_graph {
@@ -843,6 +855,7 @@ struct mce_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
+    std::vector<mce_batch_bucket> info;  // launch choice of every bucket
 };
 
 namespace {
@@ -867,6 +880,10 @@ double expected_cliques(uint32_t n, uint64_t m)
 
 struct Bucket {
     int G = 0, K = 0;
+    unsigned threads = 0;
+    uint32_t split = 0, wclass = 0;
+    bool tuned = false;
+    double tuned_ms = 0.0;
     bool smem = false;
     std::vector<uint32_t> graphs;
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
@@ -891,6 +908,118 @@ void batch_free(mce_batch *b)
 
 }  // namespace
 
+namespace {
+
+// Words-per-row class of n vertices: the smallest c with W <= 2^c.
+uint32_t words_class(uint32_t n)
+{
+    const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
+    uint32_t c = 0;
+    while ((1u << c) < W) ++c;
+    return c;
+}
+
+TuneChoice default_choice(uint32_t n, const mce_options &o)
+{
+    TuneChoice t;
+    pick_shape(n, o, t.G, t.K);
+    t.threads = o.threads_per_block ? o.threads_per_block : 256u;
+    t.split = o.split_min_p;
+    return t;
+}
+
+// Plan and capture a batch with the launch choice of every words class
+// given in `choice` (classes not in it: the defaults).
+int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
+                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out);
+
+// Milliseconds of one launch of a batch planned with `choice` (the second of
+// two launches), or a negative value if it cannot run.
+double time_choices(mce_ctx *ctx, const std::vector<mce_graph *> &graphs, const mce_options &o,
+                    const std::map<uint32_t, TuneChoice> &choice)
+{
+    mce_batch *b = nullptr;
+    if (batch_create_impl(ctx, graphs.data(), (uint32_t)graphs.size(), o, choice, &b) != MCE_OK) return -1.0;
+    double ms = -1.0;
+    if (mce_batch_run(b, nullptr) == MCE_OK && mce_batch_run(b, nullptr) == MCE_OK) {
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, b->t0, b->t1) == cudaSuccess) ms = f;
+    }
+    mce_batch_destroy(b);
+    return ms;
+}
+
+// Coordinate descent over the words classes that have no cached choice:
+// classes in decreasing order of expected work; for each, every candidate
+// (1, 2 or 4 words per lane with the fewest lanes that hold a row; 128, 256
+// or 512 threads; then the best with breadth-first split off) is timed on
+// the whole batch (up to 4096 of its graphs, sampled evenly) with the other
+// classes at their current choice, and the fastest is kept.
+void tune_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
+                const std::vector<double> &cost, std::map<uint32_t, TuneChoice> &choice)
+{
+    std::map<uint32_t, double> work;
+    std::map<uint32_t, uint32_t> members;
+    for (uint32_t i = 0; i < count; ++i) {
+        const uint32_t c = words_class(graphs[i]->n);
+        work[c] += cost[i];
+        ++members[c];
+    }
+    std::vector<mce_graph *> sample;
+    const uint32_t take = std::min<uint32_t>(count, 4096);
+    for (uint32_t j = 0; j < take; ++j) sample.push_back(graphs[(uint64_t)j * count / take]);
+    std::vector<std::pair<double, uint32_t>> order;
+    for (auto &kv : work)
+        if (!choice.count(kv.first) && members[kv.first] >= 16) order.push_back({kv.second, kv.first});
+    std::sort(order.rbegin(), order.rend());
+    for (auto &oc : order) {
+        const uint32_t c = oc.second, W = 1u << c;
+        TuneChoice best;
+        double best_ms = -1.0;
+        auto consider = [&](TuneChoice t) {
+            auto trial = choice;
+            trial[c] = t;
+            const double ms = time_choices(ctx, sample, o, trial);
+            if (ms >= 0.0 && (best_ms < 0.0 || ms < best_ms)) {
+                best_ms = ms;
+                best = t;
+            }
+        };
+        for (int K : {1, 2, 4}) {
+            uint32_t G = 1;
+            while (G * (uint32_t)K < W) G <<= 1;
+            if (G > 32) continue;
+            for (unsigned threads : {128u, 256u, 512u}) {
+                TuneChoice t;
+                t.G = (int)G;
+                t.K = K;
+                t.threads = threads;
+                t.split = o.split_min_p;
+                consider(t);
+            }
+        }
+        if (best_ms < 0.0) continue;
+        TuneChoice t = best;
+        t.split = 0xffffffffu;
+        consider(t);
+        best.tuned = true;
+        best.ms_per_graph = best_ms / (double)sample.size();
+        choice[c] = best;
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        ctx->tuned[c * 4u + o.pivot_mode] = best;
+    }
+}
+
+}  // namespace
+
+extern "C" int mce_batch_buckets(const mce_batch *b, mce_batch_bucket *out, uint32_t cap, uint32_t *count)
+{
+    if (!b || !count || (cap && !out)) return MCE_EINVAL;
+    *count = (uint32_t)b->info.size();
+    for (uint32_t i = 0; i < cap && i < b->info.size(); ++i) out[i] = b->info[i];
+    return MCE_OK;
+}
+
 extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options *opts,
                                 mce_batch **out)
 {
@@ -901,6 +1030,31 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
         return MCE_EINVAL;
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
+    for (uint32_t i = 0; i < count; ++i)
+        if (!graphs[i] || graphs[i]->ctx != ctx) return MCE_EINVAL;
+    // autotuning: cached choices first, the rest measured on this batch
+    std::map<uint32_t, TuneChoice> choice;
+    const bool forced = o.lanes_per_subtree || o.words_per_lane || o.threads_per_block || o.split_min_p;
+    if ((o.flags & MCE_AUTOTUNE) && !forced) {
+        std::vector<double> cost(count);
+        for (uint32_t i = 0; i < count; ++i) {
+            cost[i] = expected_cliques(graphs[i]->n, graphs[i]->m);
+            const uint32_t key = words_class(graphs[i]->n) * 4u + o.pivot_mode;
+            std::lock_guard<std::mutex> lk(ctx->tune_mu);
+            auto it = ctx->tuned.find(key);
+            if (it != ctx->tuned.end()) choice[words_class(graphs[i]->n)] = it->second;
+        }
+        tune_batch(ctx, graphs, count, o, cost, choice);
+    }
+    return batch_create_impl(ctx, graphs, count, o, choice, out);
+}
+
+namespace {
+
+int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
+                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out)
+{
+    *out = nullptr;
     int dev = 0, sms = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
@@ -913,7 +1067,8 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     b->count = count;
     b->n.resize(count);
 
-    // ---- plan: shape buckets, most expensive graph first
+    // ---- plan: a launch choice per graph (given per words class, else the
+    // defaults), buckets of equal choice, most expensive first
     std::vector<Bucket> buckets;
     std::vector<double> cost(count);
     uint32_t max_n = 0, max_w = 0, max_wp = 0;
@@ -921,22 +1076,35 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     for (uint32_t i = 0; i < count; ++i) {
         const mce_graph *g = graphs[i];
         if (!g || g->ctx != ctx) { delete b; return MCE_EINVAL; }
+        cost[i] = expected_cliques(g->n, g->m);
+    }
+    for (uint32_t i = 0; i < count; ++i) {
+        const mce_graph *g = graphs[i];
         b->n[i] = g->n;
         const uint32_t W = std::max<uint32_t>(1, (g->n + 31) / 32);
-        int G, K;
-        pick_shape(g->n, o, G, K);
+        const uint32_t wc = words_class(g->n);
+        auto it = choice.find(wc);
+        const TuneChoice t = it != choice.end() ? it->second : default_choice(g->n, o);
+        const int G = t.G, K = t.K;
         if ((uint32_t)(G * K) < W || !impl_for(G, K, false, (int)o.pivot_mode).run) { delete b; return MCE_EINVAL; }
         size_t bi = 0;
-        while (bi < buckets.size() && !(buckets[bi].G == G && buckets[bi].K == K)) ++bi;
+        while (bi < buckets.size() && !(buckets[bi].G == G && buckets[bi].K == K && buckets[bi].threads == t.threads &&
+                                        buckets[bi].split == t.split))
+            ++bi;
         if (bi == buckets.size()) {
             Bucket nb;
             nb.G = G;
             nb.K = K;
+            nb.threads = t.threads;
+            nb.split = t.split;
+            nb.wclass = wc;
+            nb.tuned = t.tuned;
+            nb.tuned_ms = t.ms_per_graph;
             nb.smem = G * K <= 32;
             buckets.push_back(nb);
         }
+        buckets[bi].wclass = std::max(buckets[bi].wclass, wc);
         buckets[bi].graphs.push_back(i);
-        cost[i] = expected_cliques(g->n, g->m);
         wp_of[i] = (uint32_t)(G * K);
         max_n = std::max(max_n, g->n);
         max_w = std::max(max_w, g->w);
@@ -968,7 +1136,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
         bk.impl = impl_for(bk.G, bk.K, bk.smem, (int)o.pivot_mode);
         size_t base = 0;
         for (uint32_t i : bk.graphs) base = std::max(base, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
-        unsigned threads = o.threads_per_block ? o.threads_per_block : 256u;
+        const unsigned threads = bk.threads;
         if (threads % 32 || threads > (bk.K >= 4 ? 512u : 1024u)) { rc = MCE_EINVAL; break; }
         // at most 56 KB of stack per block, so that several blocks share an SM
         size_t smem = 0;
@@ -989,6 +1157,19 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
         bk.region_off = take(bk.qstride * blocks, 256);
     }
     if (rc != MCE_OK) { delete b; return rc; }
+    for (const Bucket &bk : buckets) {
+        mce_batch_bucket bi{};
+        bi.words_class = 1u << bk.wclass;
+        bi.graphs = (uint32_t)bk.graphs.size();
+        bi.lanes_per_subtree = (uint32_t)bk.G;
+        bi.words_per_lane = (uint32_t)bk.K;
+        bi.threads_per_block = bk.threads;
+        bi.blocks = bk.shape.blocks;
+        bi.split_min_p = bk.split;
+        bi.tuned = bk.tuned ? 1u : 0u;
+        bi.tuned_ms_per_graph = bk.tuned_ms;
+        b->info.push_back(bi);
+    }
     b->dbytes = round_up(off, 256);
     rc = dalloc(ctx, &b->dmem, b->dbytes);
     if (rc != MCE_OK) { delete b; return rc; }
@@ -1056,7 +1237,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
             bp.pivot_mode = o.pivot_mode;
             bp.stack_levels = o.stack_levels ? std::min<uint32_t>(o.stack_levels, kStackDepth) : kStackDepth;
             bp.groups_per_block = bk.groups;
-            bp.split_min_p = o.split_min_p;
+            bp.split_min_p = bk.split;
             bp.split_target = bk.qcap / 2;
             bp.stack_smem_levels = bk.stack_levels;
             bp.stack_offset = bk.stack_offset;
@@ -1081,6 +1262,8 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     *out = b;
     return MCE_OK;
 }
+
+}  // namespace
 
 extern "C" int mce_batch_launch(mce_batch *b)
 {

@@ -104,3 +104,34 @@ def test_batch_of_workload_graphs(ctx, mce):
         assert (got["count"], got["hash"], got["nodes"]) == (ref["count"], ref["hash"], ref["nodes"])
     for g in graphs:
         g.free()
+
+
+def test_autotuned_batch_matches_oracle_and_reuses_choices(ctx, mce):
+    # 48 graphs of each words class 1, 2, 4 and 8 (n = 20..256), G(n, 0.3)
+    specs = [(n, synth.gnp(n, 0.3, 300 + i)) for i, n in
+             enumerate([20 + (i % 12) for i in range(48)] + [40 + (i % 24) for i in range(48)] +
+                       [70 + (i % 58) for i in range(48)] + [130 + (i % 126) for i in range(48)])]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    b = mce.Batch(ctx, graphs, mce.options(autotune=True))
+    res = b.run()
+    for (n, uv), r in list(zip(specs, res))[::7]:
+        _check(r, n, uv)
+    alone = [g.enumerate() for g in graphs]
+    assert [(r["count"], r["hash"], r["nodes"]) for r in res] == [(a["count"], a["hash"], a["nodes"]) for a in alone]
+    buckets = b.buckets()
+    assert sum(x["graphs"] for x in buckets) == len(graphs)
+    assert all(x["tuned"] == 1 for x in buckets)
+    for x in buckets:
+        assert x["lanes_per_subtree"] * x["words_per_lane"] >= x["words_class"]
+        assert x["threads_per_block"] in (128, 256, 512) and x["tuned_ms_per_graph"] > 0
+    # a second batch of the same classes takes the cached choices
+    b2 = mce.Batch(ctx, graphs[::2], mce.options(autotune=True))
+    assert {(x["lanes_per_subtree"], x["words_per_lane"], x["threads_per_block"], x["split_min_p"])
+            for x in b2.buckets()} <= {(x["lanes_per_subtree"], x["words_per_lane"], x["threads_per_block"],
+                                        x["split_min_p"]) for x in buckets}
+    r2 = b2.run()
+    assert [(r["count"], r["hash"]) for r in r2] == [(a["count"], a["hash"]) for a in alone[::2]]
+    b.close()
+    b2.close()
+    for g in graphs:
+        g.free()
