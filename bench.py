@@ -378,6 +378,62 @@ def served_form(mce, torch, ctx, specs, opts, args):
 
 # ---------------------------------------------------------------------------
 
+def table1_rows():
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "table1_random.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        t = line.split()
+        rows.append({"n": int(t[0]), "p": float(t[1]), "mu": int(t[2]),
+                     "tomita": (int(t[3]), t[4]), "nx": (int(t[5]), t[6]), "greedy": (int(t[7]), t[8])})
+    return rows
+
+
+def run_sweep(args):
+    """The paper's Table 1 grid (every shape with n <= 4096) on seeded
+    G(n, p): maximal cliques, search nodes and time per pivot rule through
+    mce_enumerate, beside the paper's steps and seconds (one CPU core, 10
+    other instances of each shape)."""
+    import torch
+
+    import paper_1801_00202_gb300 as mce
+    mce.build()
+    mce.lib()
+    ctx = mce.Context(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    out = []
+    for row in table1_rows():
+        if row["n"] > mce.MCE_NMAX:
+            continue
+        cell = {"n": row["n"], "p": row["p"], "paper_mu": row["mu"], "seeds": args.sweep_seeds}
+        mus = []
+        for pivot in ("greedy", "nx", "tomita"):
+            nodes, internal, ms = [], [], []
+            for seed in range(args.sweep_seeds):
+                g = ctx.load_edges(row["n"], synth.gnp(row["n"], row["p"], seed))
+                torch.cuda.synchronize()
+                r = g.enumerate(mce.options(pivot=pivot))
+                g.free()
+                if pivot == "greedy":
+                    mus.append(r["count"])
+                nodes.append(r["nodes"])
+                internal.append(r["internal"])
+                ms.append(r["kernel_ms"])
+            steps, secs = row[pivot]
+            cell[pivot] = {"nodes": statistics.mean(nodes), "internal_nodes": statistics.mean(internal),
+                           "ms": statistics.mean(ms), "paper_steps": steps, "paper_s": secs}
+            if not secs.startswith("<"):
+                cell[pivot]["speedup_vs_paper_core"] = float(secs) * 1e3 / statistics.mean(ms)
+        cell["mu"] = statistics.mean(mus)
+        out.append(cell)
+        print(json.dumps(cell), file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps({"sweep": "Table 1 shapes, n <= 4096", "unit": "ms per graph (whole path, device time)",
+                      "clocks": clocks.stop(), "rows": out}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -585,6 +641,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the benchmark: the paper's Table 1 grid, per pivot rule")
+    ap.add_argument("--sweep-seeds", type=int, default=3)
     ap.add_argument("--batch-graphs", type=int, default=BATCH_GRAPHS)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--served-requests", type=int, default=20000)
@@ -601,6 +660,8 @@ def main():
     select_workload(args.workload)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.sweep:
+        return run_sweep(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

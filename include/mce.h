@@ -79,6 +79,11 @@ extern "C" {
 #define MCE_PIVOT_GREEDY     0u
 #define MCE_PIVOT_GREEDY_TX  1u
 #define MCE_PIVOT_TOMITA     2u
+#define MCE_PIVOT_GREEDY_NX  3u  /* GreedyBBNX (Section 4.3): GreedyBBTX's
+                                    pivot computed as argmin over X of
+                                    |P n K(u)|, K(u) = V \ N(u), with Naude's
+                                    early exit -- the same pivot as
+                                    GREEDY_TX, so the same search tree     */
 
 /* flags */
 #define MCE_ORDER_IDENTITY   0x1u  /* skip the maximum-degree-first ordering

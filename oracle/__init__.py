@@ -32,7 +32,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-MODES = {"greedy": 0, "tx": 1, "tomita": 2}
+MODES = {"greedy": 0, "tx": 1, "tomita": 2, "nx": 3}
 
 
 def build(force: bool = False) -> str:

@@ -26,6 +26,10 @@
  *       0 GreedyBB    p = first vertex of X in the order, else first of P;
  *       1 GreedyBBTX  p = argmax_{u in X} |P n N(u)|, else first of P;
  *       2 TomitaBB    p = argmax_{u in P u X} |P n N(u)|;
+ *       3 GreedyBBNX  p = argmin_{u in X} |P n K(u)|, K(u) = V \ N(u) (u
+ *                     included), else first of P; a candidate's count stops
+ *                     as soon as it cannot beat the best so far (Naude's
+ *                     early exit, as described in Section 4.3);
  *     argmax ties go to the vertex earliest in the order (Section 4.3).
  *     Its sets are sorted arrays of positions, so "first in the order" is
  *     element 0 -- no bitsets.
@@ -292,6 +296,24 @@ static void bk_ordered(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t
                 uint32_t du; const uint32_t *nu = nbr(r, X[i], &du);
                 uint32_t c = set_and_count(P, np, nu, du);
                 if (i == 0 || c > best_c) { best_c = c; p = X[i]; }
+            }
+        } else {
+            p = P[0];
+        }
+    } else if (r->mode == 3) {
+        if (nx) {
+            /* count P n K(u) by walking P against the sorted N(u); a
+             * candidate is dropped once its count reaches the best one's */
+            uint32_t best_k = UINT32_MAX; p = X[0];
+            for (uint32_t i = 0; i < nx; ++i) {
+                uint32_t du; const uint32_t *nu = nbr(r, X[i], &du);
+                uint32_t k = 0, a = 0, b = 0;
+                while (a < np && k < best_k) {
+                    while (b < du && nu[b] < P[a]) ++b;
+                    if (b >= du || nu[b] != P[a]) ++k;  /* P[a] not a neighbour of X[i] */
+                    ++a;
+                }
+                if (a == np && k < best_k) { best_k = k; p = X[i]; }
             }
         } else {
             p = P[0];

@@ -28,8 +28,8 @@ MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETRUNC = -1, -2, -3, -4
 MCE_ETIMEOUT, MCE_EOVERFLOW, MCE_ENOTIMPL = -5, -6, -7
 MCE_NMAX = 4096
 
-MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA = 0, 1, 2
-PIVOTS = {"greedy": 0, "tx": 1, "tomita": 2}
+MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA, MCE_PIVOT_GREEDY_NX = 0, 1, 2, 3
+PIVOTS = {"greedy": 0, "tx": 1, "tomita": 2, "nx": 3}
 MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED, MCE_AUTOTUNE = 0x1, 0x2, 0x4, 0x8
 
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3

@@ -52,6 +52,7 @@ mce_options defaults(const mce_options *o)
 
 SearchImpl impl_for(int G, int K, bool smem, int pivot, bool list = false)
 {
+    if (pivot == MCE_PIVOT_GREEDY_NX) pivot = MCE_PIVOT_GREEDY_TX;  // the TX kernels, early exit on
 #define MCE_IMPL_CASE(g, k)                                                                                \
     case g * 8 + k:                                                                                        \
         return list ? search_list_impl_##g##_##k(smem, pivot) : search_impl_##g##_##k(smem, pivot);
@@ -138,7 +139,7 @@ unsigned default_threads(uint32_t n, int K)
 // form keeps blocks small so that several requests share an SM).
 int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(size_t)0)
 {
-    if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
+    if (o.pivot_mode > MCE_PIVOT_GREEDY_NX || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
         return MCE_EINVAL;
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
     int G, K;
@@ -1027,7 +1028,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
     *out = nullptr;
     DevicePick pick(ctx->device);
     const mce_options o = defaults(opts);
-    if (o.pivot_mode > MCE_PIVOT_TOMITA || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
+    if (o.pivot_mode > MCE_PIVOT_GREEDY_NX || o.stack_levels > (uint32_t)kStackDepth || o.queue_log2 > 24)
         return MCE_EINVAL;
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
     for (uint32_t i = 0; i < count; ++i)

@@ -1307,6 +1307,17 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             }
             int best = -1;
             pc = (PIVOT == MCE_PIVOT_GREEDY_TX) ? fp : -1;  // X' empty: first of P'
+            // GreedyBBNX (the TX kernel with pivot_mode NX): Naude's early exit.
+            // A candidate's count is one group-wide popcount here, so the
+            // exit is at candidate level: once a candidate covers all of P'
+            // (|P' n K(u)| = 0), no later one can beat it and the scan stops.
+            const bool nx = PIVOT == MCE_PIVOT_GREEDY_TX && prm.pivot_mode == MCE_PIVOT_GREEDY_NX;
+            int npc = 0;
+            if (nx) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) npc += __popc(Pc[k]);
+                npc = g.sum(npc);
+            }
             for (;;) {
                 uint32_t o = 0;
 #pragma unroll
@@ -1327,6 +1338,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                         pc = u;
                     }
                     g.clear(cand, u);
+                    if (nx && best == npc) {
+#pragma unroll
+                        for (int k = 0; k < K; ++k) cand[k] = 0u;
+                    }
                 }
             }
         }

@@ -48,7 +48,7 @@ def mixed_specs():
     return specs
 
 
-@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita"])
+@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita", "nx"])
 def test_mixed_batch_matches_oracle(ctx, mce, mode):
     specs = mixed_specs()
     graphs = [ctx.load_edges(n, uv) for n, uv in specs]

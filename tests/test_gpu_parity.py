@@ -71,7 +71,7 @@ def test_random_graph(ctx, mce, n, p, seed):
     expect_equal(run_host(ctx, mce, n, uv), n, uv, what=f"G({n},{p}) seed {seed}")
 
 
-@pytest.mark.parametrize("mode", ["tx", "tomita"])
+@pytest.mark.parametrize("mode", ["tx", "tomita", "nx"])
 @pytest.mark.parametrize("n,p,seed", [(50, 0.5, 30), (100, 0.5, 0), (200, 0.3, 31), (700, 0.1, 32)])
 def test_pivot_rules(ctx, mce, mode, n, p, seed):
     uv = synth.gnp(n, p, seed)

@@ -79,7 +79,8 @@ def check_all_against(n, uv, cliques):
     for res in (oracle.tomita(n, uv, listing=True),
                 oracle.ordered(n, uv, "greedy", listing=True),
                 oracle.ordered(n, uv, "tx", listing=True),
-                oracle.ordered(n, uv, "tomita", listing=True)):
+                oracle.ordered(n, uv, "tomita", listing=True),
+                oracle.ordered(n, uv, "nx", listing=True)):
         assert res["count"] == cnt
         assert np.array_equal(res["hist"], hist)
         assert res["hash"] == h
@@ -131,7 +132,7 @@ def test_random_against_brute_force(n, p, seed):
 @pytest.mark.parametrize("k", range(1, 9))
 def test_moon_moser(k):
     n = 3 * k
-    for mode in ("greedy", "tx", "tomita"):
+    for mode in ("greedy", "tx", "tomita", "nx"):
         r = oracle.ordered(n, synth.moon_moser(k), mode)
         assert r["count"] == 3 ** k
         assert r["hist"][k] == 3 ** k and r["hist"].sum() == 3 ** k
@@ -356,3 +357,57 @@ def test_table1_mean_mu(n, p, mu):
     mean = float(np.mean(counts))
     assert abs(mean / mu - 1.0) < 0.12
     assert abs(mean / synth.expected_maximal_cliques(n, p) - 1.0) < 0.12
+
+
+# --- GreedyBBNX picks GreedyBBTX's pivot ------------------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_nx_pivot_is_tx_pivot(seed):
+    # For u in X (disjoint from P), |P n K(u)| = |P| - |P n N(u)|, so the
+    # argmin of NX is TX's argmax with the same earliest-on-ties rule, and
+    # the early exit only drops candidates that cannot win: every traced
+    # node must pick the same pivot and branching set, and the trees agree.
+    n, p = 16 + 9 * seed, 0.25 + 0.07 * seed
+    uv = synth.gnp(n, p, 700 + seed)
+    a = oracle.ordered(n, uv, "nx", trace_cap=4096)
+    b = oracle.ordered(n, uv, "tx", trace_cap=4096)
+    assert a["trace"] == b["trace"]
+    assert (a["nodes"], a["internal"], a["dead_ends"]) == (b["nodes"], b["internal"], b["dead_ends"])
+    ref = oracle.tomita(n, uv)
+    assert (a["count"], a["hash"]) == (ref["count"], ref["hash"])
+
+
+
+# --- the paper's step counts (Table 1) ----------------------------------------
+
+def _table1():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "table1_random.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        t = line.split()
+        rows[(int(t[0]), float(t[1]))] = {"mu": int(t[2]), "tomita": int(t[3]), "nx": int(t[5]), "greedy": int(t[7])}
+    return rows
+
+
+@pytest.mark.parametrize("n,p", [(100, 0.6), (300, 0.1), (300, 0.2), (300, 0.3), (500, 0.1), (500, 0.2),
+                                 (700, 0.1), (1000, 0.1)])
+def test_steps_per_clique_match_table1(n, p):
+    # Table 1 reports, per shape G(n, p), the mean maximal cliques mu and the
+    # mean search steps of GreedyBB, GreedyBBNX and TomitaBB over 10
+    # unpublished instances.  A step is a call with P non-empty (our
+    # "internal" node): the steps-per-clique ratio of the oracle's Alg. 4
+    # tree on 3 seeded instances must match the paper's within 6 %, and the
+    # three pivot rules must keep the paper's order (TomitaBB < NX < GreedyBB).
+    paper = _table1()[(n, p)]
+    got = {m: [0, 0] for m in ("greedy", "nx", "tomita")}
+    for seed in range(3):
+        uv = synth.gnp(n, p, seed)
+        for m in got:
+            r = oracle.ordered(n, uv, m)
+            got[m][0] += r["internal"]
+            got[m][1] += r["count"]
+    for m, (steps, mu) in got.items():
+        ours, theirs = steps / mu, paper[m] / paper["mu"]
+        assert abs(ours / theirs - 1.0) < 0.06, (m, ours, theirs)
+    assert got["tomita"][0] <= got["nx"][0] <= got["greedy"][0]
