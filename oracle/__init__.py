@@ -62,6 +62,10 @@ def _load():
         lib.oracle_ordered.restype = C.c_int
         lib.oracle_ordered.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, u32p, u64p, u64p,
                                        u32p, C.c_uint64, u64p, i32p, C.c_uint64, u64p]
+        lib.oracle_degeneracy_order.restype = None
+        lib.oracle_degeneracy_order.argtypes = [C.c_uint32, u32p, u32p, u32p]
+        lib.oracle_outer.restype = C.c_int
+        lib.oracle_outer.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, u64p, u64p, u32p, C.c_uint64, u64p]
         _lib = lib
     return _lib
 
@@ -187,3 +191,40 @@ def mix64(z: int) -> int:
 def clique_hash(labels) -> int:
     a = np.ascontiguousarray(np.asarray(labels, dtype=np.uint32).reshape(-1))
     return int(_load().oracle_clique_hash(_p(a if a.size else np.zeros(1, np.uint32), C.c_uint32), a.size))
+
+
+def degeneracy_order(n: int, uv) -> np.ndarray:
+    """Alg. 3's outer order: minimum remaining degree first, smallest label
+    on ties."""
+    off, adj = csr(n, uv)
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    _load().oracle_degeneracy_order(n, _p(off, C.c_uint32), _p(adj if adj.size else np.zeros(1, np.uint32), C.c_uint32),
+                                    _p(out, C.c_uint32))
+    return out[:n]
+
+
+def outer(n: int, uv, mode: str = "greedy", listing: bool = False, list_cap: int = 1 << 22):
+    """Alg. 3: for every vertex v in degeneracy order, the ordered search
+    (Alg. 4, pivot rule ``mode``) on G[{v} u N(v)] from R = {v}, P = later
+    neighbours, X = earlier neighbours.  Returns the result dict plus the
+    outer ``order``."""
+    lib = _load()
+    off, adj = csr(n, uv)
+    stats = np.zeros(5, dtype=np.uint64)
+    hist = np.zeros(n + 1, dtype=np.uint64)
+    lst = np.zeros(list_cap if listing else 1, dtype=np.uint32)
+    used = np.zeros(1, dtype=np.uint64)
+    oout = np.zeros(max(n, 1), dtype=np.uint32)
+    rc = lib.oracle_outer(n, _p(off, C.c_uint32), _p(adj if adj.size else np.zeros(1, np.uint32), C.c_uint32),
+                          MODES[mode], _p(oout, C.c_uint32), _p(stats, C.c_uint64), _p(hist, C.c_uint64),
+                          _p(lst, C.c_uint32) if listing else None, lst.size, _p(used, C.c_uint64))
+    if rc < 0:
+        raise MemoryError("oracle ran out of memory")
+    if listing and int(used[0]) > lst.size:
+        return outer(n, uv, mode, True, int(used[0]) + 16)
+    res = _result(stats, hist, n)
+    res["order"] = oout[:n].copy()
+    if listing:
+        res["listing"] = _unpack_listing(lst, int(used[0]))
+    return res
+

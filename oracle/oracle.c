@@ -492,3 +492,124 @@ done:
     run_free(&r);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 3. The outer loop of Alg. 3 for large sparse graphs.                      */
+
+/* Degeneracy ordering (Section 3.3): repeatedly remove a vertex of minimum
+ * degree in the remaining graph; ties go to the smallest label. */
+void oracle_degeneracy_order(uint32_t n, const uint32_t *off, const uint32_t *adj, uint32_t *order)
+{
+    uint32_t *deg = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    unsigned char *gone = (unsigned char *)calloc(n ? n : 1, 1);
+    for (uint32_t v = 0; v < n; ++v) deg[v] = off[v + 1] - off[v];
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t best = 0; int have = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            if (gone[v]) continue;
+            if (!have || deg[v] < deg[best]) { best = v; have = 1; }
+        }
+        order[i] = best;
+        gone[best] = 1;
+        for (uint32_t e = off[best]; e < off[best + 1]; ++e)
+            if (!gone[adj[e]]) deg[adj[e]]--;
+    }
+    free(deg);
+    free(gone);
+}
+
+/* Alg. 3 with the paper's ordered search inside.  For every vertex v, in
+ * degeneracy order: the subproblem graph H = G[{v} u N(v)], its vertices
+ * taken in increasing label, is ordered maximum-degree-first and renumbered
+ * (Section 4.2), and BKPivotOrdered (Alg. 4, pivot rule `mode`) runs from
+ * R = {v}, P = the neighbours of v after it in the degeneracy order, X = the
+ * neighbours before it.  Every maximal clique is reported once, in the
+ * subproblem of its vertex earliest in the degeneracy order.  `deg_order`
+ * (optional, n entries) receives the outer order.  Adjacency lists must be
+ * sorted.  stats/hist/list as for oracle_ordered. */
+int oracle_outer(uint32_t n, const uint32_t *off, const uint32_t *adj, int mode, uint32_t *deg_order,
+                 uint64_t *stats, uint64_t *hist, uint32_t *list, uint64_t list_cap, uint64_t *list_used)
+{
+    run_t r;
+    int rc = run_init(&r, n, hist, list, list_cap);
+    size_t nn = (size_t)(n ? n : 1);
+    uint32_t maxd = 0;
+    for (uint32_t v = 0; v < n; ++v)
+        if (off[v + 1] - off[v] > maxd) maxd = off[v + 1] - off[v];
+    size_t hn = (size_t)maxd + 1;                       /* vertices of a subproblem */
+    uint32_t *dord = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    uint32_t *dpos = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    uint32_t *U = (uint32_t *)malloc(hn * sizeof(uint32_t));
+    uint32_t *hoff = (uint32_t *)malloc((hn + 1) * sizeof(uint32_t));
+    uint32_t *hadj = (uint32_t *)malloc(hn * hn * sizeof(uint32_t));
+    uint32_t *hord = (uint32_t *)malloc(hn * sizeof(uint32_t));
+    uint32_t *hpos = (uint32_t *)malloc(hn * sizeof(uint32_t));
+    uint32_t *roff = (uint32_t *)malloc((hn + 1) * sizeof(uint32_t));
+    uint32_t *radj = (uint32_t *)malloc(hn * hn * sizeof(uint32_t));
+    uint32_t *lab = (uint32_t *)malloc(hn * sizeof(uint32_t));
+    uint32_t *P = (uint32_t *)malloc((nn + 1) * sizeof(uint32_t));
+    uint32_t *X = (uint32_t *)malloc((nn + 1) * sizeof(uint32_t));
+    if (rc || !dord || !dpos || !U || !hoff || !hadj || !hord || !hpos || !roff || !radj || !lab || !P || !X) {
+        rc = -2;
+        goto done;
+    }
+    oracle_degeneracy_order(n, off, adj, dord);
+    if (deg_order) memcpy(deg_order, dord, (size_t)n * sizeof(uint32_t));
+    for (uint32_t i = 0; i < n; ++i) dpos[dord[i]] = i;
+    r.mode = mode;
+
+    for (uint32_t i = 0; i < n && !r.oom; ++i) {
+        const uint32_t v = dord[i];
+        /* U = {v} u N(v) in increasing label */
+        uint32_t h = 0, e = off[v];
+        while (e < off[v + 1] && adj[e] < v) U[h++] = adj[e++];
+        U[h++] = v;
+        while (e < off[v + 1]) U[h++] = adj[e++];
+        /* H's adjacency in local indices: N(a) n U for every a in U */
+        hoff[0] = 0;
+        for (uint32_t a = 0; a < h; ++a) {
+            uint32_t k = hoff[a], x = off[U[a]], y = 0;
+            while (x < off[U[a] + 1] && y < h) {
+                if (adj[x] < U[y]) ++x;
+                else if (adj[x] > U[y]) ++y;
+                else { hadj[k++] = y; ++x; ++y; }
+            }
+            hoff[a + 1] = k;
+        }
+        /* maximum-degree-first order of H and renumbering by position */
+        oracle_mdf_order(h, hoff, hadj, hord);
+        for (uint32_t j = 0; j < h; ++j) hpos[hord[j]] = j;
+        roff[0] = 0;
+        for (uint32_t j = 0; j < h; ++j) {
+            uint32_t a = hord[j], k = roff[j];
+            for (uint32_t t = hoff[a]; t < hoff[a + 1]; ++t) radj[k++] = hpos[hadj[t]];
+            roff[j + 1] = k;
+            for (uint32_t s = roff[j] + 1; s < k; ++s) {
+                uint32_t x = radj[s], b = s;
+                while (b > roff[j] && radj[b - 1] > x) { radj[b] = radj[b - 1]; --b; }
+                radj[b] = x;
+            }
+            lab[j] = U[a];
+        }
+        /* the root: R = {v}, P = later neighbours, X = earlier ones, as
+         * sorted position lists */
+        uint32_t np = 0, nx = 0, pv = 0;
+        for (uint32_t j = 0; j < h; ++j) {
+            const uint32_t u = lab[j];
+            if (u == v) pv = j;
+            else if (dpos[u] > i) P[np++] = j;
+            else X[nx++] = j;
+        }
+        r.off = roff; r.adj = radj; r.label = lab;
+        r.R[0] = pv;
+        bk_ordered(&r, P, np, X, nx, 1);
+    }
+    rc = r.oom ? -2 : 0;
+    run_stats(&r, stats, list_used);
+done:
+    free(dord); free(dpos); free(U); free(hoff); free(hadj); free(hord); free(hpos);
+    free(roff); free(radj); free(lab); free(P); free(X);
+    run_free(&r);
+    return rc;
+}
+

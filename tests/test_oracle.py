@@ -411,3 +411,69 @@ def test_steps_per_clique_match_table1(n, p):
         ours, theirs = steps / mu, paper[m] / paper["mu"]
         assert abs(ours / theirs - 1.0) < 0.06, (m, ours, theirs)
     assert got["tomita"][0] <= got["nx"][0] <= got["greedy"][0]
+
+
+# --- Alg. 3: degeneracy-ordered outer loop ----------------------------------
+
+def _remaining_degree_check(n, uv, order):
+    adj = [set() for _ in range(n)]
+    for a, b in uv:
+        adj[int(a)].add(int(b))
+        adj[int(b)].add(int(a))
+    left = set(range(n))
+    for v in order:
+        v = int(v)
+        deg = {u: len(adj[u] & left) for u in left}
+        dmin = min(deg.values())
+        assert deg[v] == dmin and v == min(u for u in left if deg[u] == dmin)
+        left.remove(v)
+
+
+@pytest.mark.parametrize("n,p,seed", [(20, 0.3, 1), (40, 0.15, 2), (60, 0.5, 3)])
+def test_degeneracy_order_definition(n, p, seed):
+    uv = synth.gnp(n, p, seed)
+    _remaining_degree_check(n, uv, oracle.degeneracy_order(n, uv))
+
+
+def test_degeneracy_order_bounds_later_neighbours_by_the_core_number():
+    nx = pytest.importorskip("networkx")
+    n, uv = 300, synth.gnp(300, 0.05, 9)
+    order = oracle.degeneracy_order(n, uv)
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n)
+    later = np.zeros(n, dtype=np.int64)
+    for a, b in uv:
+        later[a if pos[a] < pos[b] else b] += 1
+    g = nx.Graph()
+    g.add_nodes_from(range(n))
+    g.add_edges_from(uv.tolist())
+    assert later.max() == max(nx.core_number(g).values())
+
+
+@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita", "nx"])
+@pytest.mark.parametrize("n,p,seed", [(16, 0.5, 1), (80, 0.1, 2), (300, 0.03, 3), (120, 0.3, 4)])
+def test_outer_loop_lists_the_maximal_cliques(mode, n, p, seed):
+    uv = synth.gnp(n, p, seed)
+    a = oracle.outer(n, uv, mode, listing=True)
+    ref = oracle.tomita(n, uv, listing=True)
+    assert (a["count"], a["hash"]) == (ref["count"], ref["hash"])
+    assert np.array_equal(a["hist"], ref["hist"])
+    assert a["listing"] == ref["listing"]
+    assert a["nodes"] == a["count"] + a["internal"] + a["dead_ends"]
+
+
+@pytest.mark.parametrize("n", [2, 5, 9, 30])
+def test_outer_loop_tree_on_complete_and_empty_graphs(n):
+    # K_n: v_0's subproblem is a chain of n calls; every later v_i has its
+    # earlier neighbour v_0 in X, which pivots away all of P (one internal
+    # call) except the last, whose P is empty (one dead end).
+    a = oracle.outer(n, synth.complete(n))
+    assert (a["count"], a["nodes"], a["internal"], a["dead_ends"]) == (1, 2 * n - 1, 2 * n - 3, 1)
+    e = oracle.outer(n, synth.empty(n))
+    assert (e["count"], e["nodes"], e["internal"], e["dead_ends"]) == (n, n, 0, 0)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_outer_loop_moon_moser(k):
+    a = oracle.outer(3 * k, synth.moon_moser(k))
+    assert a["count"] == 3 ** k and int(a["hist"][k]) == 3 ** k
