@@ -66,7 +66,12 @@ extern "C" {
 #define MCE_EOVERFLOW -6   /* the device work queue overflowed               */
 #define MCE_ENOTIMPL  -7   /* option combination not implemented             */
 
-#define MCE_NMAX 4096u     /* largest supported number of vertices           */
+#define MCE_NMAX 4096u     /* largest number of vertices on the bitset path  */
+#define MCE_NMAX_SPARSE 65535u  /* largest graph mce_load_edges accepts:
+                              above MCE_NMAX a graph is held as sorted
+                              adjacency lists and enumerated by the outer
+                              loop of Alg. 3 (see MCE_OUTER), which needs
+                              every degree below MCE_NMAX                 */
 
 /* ----------------------------------------------------------------------- */
 /* Options                                                                   */
@@ -98,6 +103,19 @@ extern "C" {
                                       of every words-per-row class on the
                                       batch's own graphs (see
                                       mce_batch_create)                      */
+#define MCE_OUTER            0x10u /* mce_enumerate: Alg. 3's outer loop (the
+                                      only path for n > MCE_NMAX): for every
+                                      vertex v in degeneracy order (minimum
+                                      remaining degree first, smallest label
+                                      on ties), the search of Alg. 4 on
+                                      G[{v} u N(v)] -- ordered maximum-degree-
+                                      first -- from R = {v}, P = the
+                                      neighbours after v, X = those before;
+                                      all subproblems run as one batch.
+                                      Results equal the plain path's; node
+                                      counters are this loop's (the sum of
+                                      the subproblem trees).  Not with
+                                      MCE_LIST.                             */
 #define MCE_LIST_SORTED      0x4u  /* MCE_LIST with the cliques in
                                       lexicographic order (the problem's
                                       output, Section 2: all maximal cliques) */

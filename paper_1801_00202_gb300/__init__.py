@@ -26,11 +26,11 @@ from .build import LIB as _LIB_PATH, build  # noqa: F401
 MCE_OK, MCE_PENDING = 0, 1
 MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETRUNC = -1, -2, -3, -4
 MCE_ETIMEOUT, MCE_EOVERFLOW, MCE_ENOTIMPL = -5, -6, -7
-MCE_NMAX = 4096
+MCE_NMAX, MCE_NMAX_SPARSE = 4096, 65535
 
 MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA, MCE_PIVOT_GREEDY_NX = 0, 1, 2, 3
 PIVOTS = {"greedy": 0, "tx": 1, "tomita": 2, "nx": 3}
-MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED, MCE_AUTOTUNE = 0x1, 0x2, 0x4, 0x8
+MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED, MCE_AUTOTUNE, MCE_OUTER = 0x1, 0x2, 0x4, 0x8, 0x10
 
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
 MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
@@ -73,10 +73,12 @@ class Result(C.Structure):
 
 def options(pivot: str | int = "greedy", identity_order: bool = False, lanes: int = 0, words: int = 0,
             blocks: int = 0, threads: int = 0, timeout_ns: int = 0, stack_levels: int = 0,
-            queue_log2: int = 0, split_min_p: int = 0, flags: int = 0, autotune: bool = False) -> Options:
+            queue_log2: int = 0, split_min_p: int = 0, flags: int = 0, autotune: bool = False,
+            outer: bool = False) -> Options:
     o = Options()
     o.pivot_mode = PIVOTS[pivot] if isinstance(pivot, str) else int(pivot)
-    o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0) | (MCE_AUTOTUNE if autotune else 0)
+    o.flags = flags | (MCE_ORDER_IDENTITY if identity_order else 0) | (MCE_AUTOTUNE if autotune else 0) | \
+        (MCE_OUTER if outer else 0)
     o.lanes_per_subtree, o.words_per_lane = lanes, words
     o.blocks, o.threads_per_block = blocks, threads
     o.timeout_ns, o.stack_levels, o.queue_log2 = timeout_ns, stack_levels, queue_log2
@@ -400,6 +402,7 @@ class Batch:
     """mce_batch: graphs planned once and captured into one CUDA graph."""
 
     def __init__(self, ctx: Context, graphs, opts: Options | None = None):
+        self.handle = None
         self.ctx, self.graphs = ctx, list(graphs)
         arr = (C.c_void_p * max(len(self.graphs), 1))(*[g.handle for g in self.graphs])
         h = C.c_void_p()

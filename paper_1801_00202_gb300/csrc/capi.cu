@@ -420,9 +420,17 @@ struct mce_ctx {
 struct mce_graph {
     mce_ctx *ctx = nullptr;
     uint32_t n = 0, w = 0;
-    uint32_t *d_rows = nullptr;
+    uint32_t *d_rows = nullptr;  // bitset (null for a graph held only as CSR)
     uint64_t bytes = 0;
     uint64_t m = 0;  // edges (as given: an estimate when duplicates were passed)
+    // CSR (sorted lists) for the outer loop of Alg. 3: built at load for
+    // n > MCE_NMAX, else on first use
+    uint32_t *d_off = nullptr, *d_adj = nullptr;
+    uint64_t csr_bytes = 0;
+    // a subproblem of the outer loop (library-internal graphs only)
+    const uint32_t *label = nullptr, *root = nullptr;
+    uint32_t rv = 0;
+    double cost_hint = 0.0;
 };
 
 namespace {
@@ -551,11 +559,64 @@ int finish_load(mce_ctx *ctx, mce_graph *g, uint64_t *d_status, mce_graph **out)
 
 }  // namespace
 
+namespace {
+
+// A graph beyond the bitset path: CSR only (Alg. 3's outer loop).
+int load_edges_csr(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint64_t m, mce_graph **out)
+{
+    mce_graph *g = new (std::nothrow) mce_graph;
+    if (!g) return MCE_ENOMEM;
+    g->ctx = ctx;
+    g->n = n;
+    g->w = (n + 31) / 32;
+    g->m = m;
+    size_t tb = 0;
+    outer_csr_from_edges_bytes(n, m, &tb);
+    uint32_t *d_uv = nullptr;
+    uint64_t *d_status = nullptr;
+    void *temp = nullptr;
+    g->csr_bytes = round_up(((uint64_t)n + 1) * 4, 256) + round_up(std::max<uint64_t>(2 * m, 1) * 4, 256);
+    int rc = dalloc(ctx, (void **)&g->d_off, g->csr_bytes);
+    if (rc == MCE_OK) rc = dalloc(ctx, (void **)&d_status, 64);
+    if (rc == MCE_OK && m) rc = dalloc(ctx, (void **)&d_uv, m * 8);
+    if (rc == MCE_OK) rc = dalloc(ctx, &temp, tb);
+    cudaError_t e = cudaSuccess;
+    if (rc == MCE_OK) {
+        g->d_adj = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(g->d_off) +
+                                                round_up(((uint64_t)n + 1) * 4, 256));
+        e = cudaMemsetAsync(d_status, 0, 64, ctx->stream);
+        if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_uv, uv, m * 8, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = outer_csr_from_edges(n, m, d_uv, temp, tb, g->d_off, g->d_adj, d_status, ctx->stream);
+        if (e != cudaSuccess) rc = MCE_ECUDA;
+    }
+    dfree(ctx, temp, tb);
+    dfree(ctx, d_uv, m * 8);
+    uint64_t st = 0;
+    if (rc == MCE_OK) {
+        e = cudaMemcpyAsync(&st, d_status + MCE_OUT_STATUS, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = MCE_ECUDA;
+        else if (st) rc = (int)(int64_t)st;
+    }
+    dfree(ctx, d_status, 64);
+    if (rc != MCE_OK) {
+        dfree(ctx, g->d_off, g->csr_bytes);
+        cudaStreamSynchronize(ctx->stream);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return MCE_OK;
+}
+
+}  // namespace
+
 extern "C" int mce_load_edges(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint64_t m, mce_graph **out)
 {
-    if (!ctx || !out || n > MCE_NMAX || (m && !uv)) return MCE_EINVAL;
+    if (!ctx || !out || n > MCE_NMAX_SPARSE || (m && !uv)) return MCE_EINVAL;
     *out = nullptr;
     DevicePick pick(ctx->device);
+    if (n > MCE_NMAX) return load_edges_csr(ctx, n, uv, m, out);
     mce_graph *g = new (std::nothrow) mce_graph;
     if (!g) return MCE_ENOMEM;
     g->ctx = ctx;
@@ -626,6 +687,7 @@ extern "C" void mce_graph_free(mce_graph *g)
     if (!g) return;
     DevicePick pick(g->ctx->device);
     dfree(g->ctx, g->d_rows, g->bytes);
+    dfree(g->ctx, g->d_off, g->csr_bytes);
     cudaStreamSynchronize(g->ctx->stream);
     delete g;
 }
@@ -658,12 +720,21 @@ namespace {
 int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0);
 }
 
+namespace {
+int enumerate_outer(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0);
+}
+
 extern "C" int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res)
 {
     if (!g || !res) return MCE_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
     DevicePick pick(g->ctx->device);
     mce_options o = defaults(opts);
+    if (!g->d_rows || ((o.flags & MCE_OUTER) && g->n > 0)) {
+        if (o.flags & kListFlags) return MCE_ENOTIMPL;
+        if (o.pivot_mode > MCE_PIVOT_GREEDY_NX) return MCE_EINVAL;
+        return enumerate_outer(g, o, res, t0);
+    }
     int rc = enumerate_once(g, o, res, t0);
     // a queue overflow leaves no partial state behind: retry with 16x the slots
     for (int tries = 0; rc == MCE_EOVERFLOW && tries < 2; ++tries) {
@@ -857,6 +928,7 @@ struct mce_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     std::vector<mce_batch_bucket> info;  // launch choice of every bucket
+    const BatchGraph *d_table = nullptr;
 };
 
 namespace {
@@ -1032,7 +1104,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
         return MCE_EINVAL;
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;
     for (uint32_t i = 0; i < count; ++i)
-        if (!graphs[i] || graphs[i]->ctx != ctx) return MCE_EINVAL;
+        if (!graphs[i] || graphs[i]->ctx != ctx || !graphs[i]->d_rows) return MCE_EINVAL;
     // autotuning: cached choices first, the rest measured on this batch
     std::map<uint32_t, TuneChoice> choice;
     const bool forced = o.lanes_per_subtree || o.words_per_lane || o.threads_per_block || o.split_min_p;
@@ -1076,8 +1148,8 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
     std::vector<uint32_t> wp_of(count);
     for (uint32_t i = 0; i < count; ++i) {
         const mce_graph *g = graphs[i];
-        if (!g || g->ctx != ctx) { delete b; return MCE_EINVAL; }
-        cost[i] = expected_cliques(g->n, g->m);
+        if (!g || g->ctx != ctx || !g->d_rows) { delete b; return MCE_EINVAL; }
+        cost[i] = g->cost_hint > 0.0 ? g->cost_hint : expected_cliques(g->n, g->m);
     }
     for (uint32_t i = 0; i < count; ++i) {
         const mce_graph *g = graphs[i];
@@ -1189,6 +1261,10 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         t.w = graphs[i]->w;
         t.wp = wp_of[i];
         t.pad = 0;
+        t.label = graphs[i]->label;
+        t.root = graphs[i]->root;
+        t.rv = graphs[i]->rv;
+        t.pad2 = 0;
     }
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaSuccess;
@@ -1215,6 +1291,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
     // ---- capture: clear results, order, renumber, then one persistent
     // search launch per shape, forked so their tails overlap
     const BatchGraph *d_table = reinterpret_cast<const BatchGraph *>(base + table_off);
+    b->d_table = d_table;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t ce = cudaMemsetAsync(b->d_out, 0, b->out_words * 8, s);
@@ -1262,6 +1339,148 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
     b->h_out.assign(b->out_words, 0);
     *out = b;
     return MCE_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Alg. 3's outer loop: CSR, degeneracy order, one subproblem per vertex
+// (rows, labels and root sets extracted on the device), all subproblems
+// searched as one batch, their results summed.
+int enumerate_outer(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0)
+{
+    mce_ctx *ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const uint32_t n = g->n;
+    int rc = MCE_OK;
+    cudaError_t e = cudaSuccess;
+    if (!g->d_off) {  // bitset graph: CSR built once from its rows
+        size_t need = 0;
+        outer_csr_from_rows(n, g->w, g->d_rows, nullptr, nullptr, nullptr, 0, &need, s);
+        void *temp = nullptr;
+        uint32_t *off = nullptr;
+        const uint64_t offb = round_up(((uint64_t)n + 1) * 4, 256);
+        rc = dalloc(ctx, &temp, need);
+        if (rc == MCE_OK) rc = dalloc(ctx, (void **)&off, offb);
+        if (rc == MCE_OK) e = outer_csr_from_rows(n, g->w, g->d_rows, off, nullptr, temp, need, nullptr, s);
+        uint32_t total = 0;
+        if (rc == MCE_OK && e == cudaSuccess) e = cudaMemcpyAsync(&total, off + n, 4, cudaMemcpyDeviceToHost, s);
+        if (rc == MCE_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (rc == MCE_OK && e == cudaSuccess) {
+            g->csr_bytes = offb + round_up(std::max<uint64_t>(total, 1) * 4, 256);
+            rc = dalloc(ctx, (void **)&g->d_off, g->csr_bytes);
+            if (rc == MCE_OK) {
+                g->d_adj = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(g->d_off) + offb);
+                e = outer_csr_from_rows(n, g->w, g->d_rows, g->d_off, g->d_adj, temp, need, nullptr, s);
+            } else {
+                g->d_off = nullptr;
+            }
+        }
+        dfree(ctx, off, offb, s);
+        dfree(ctx, temp, need, s);
+        if (rc == MCE_OK && e != cudaSuccess) rc = MCE_ECUDA;
+        if (rc != MCE_OK) {
+            cudaStreamSynchronize(s);
+            return rc;
+        }
+    }
+    // degrees (host copy of the offsets) and the degeneracy order
+    std::vector<uint32_t> off(n + 1), order(n);
+    e = cudaMemcpyAsync(off.data(), g->d_off, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return MCE_ECUDA;
+    uint32_t maxd = 0;
+    for (uint32_t v = 0; v < n; ++v) maxd = std::max(maxd, off[v + 1] - off[v]);
+    if (maxd + 1 > MCE_NMAX) return MCE_ENOTIMPL;  // a subproblem beyond the bitset path
+    uint32_t *d_ord = nullptr;
+    rc = dalloc(ctx, (void **)&d_ord, ((size_t)n * 2 + 64) * 4, s);
+    if (rc != MCE_OK) return rc;
+    uint32_t *d_pos = d_ord + n + 32;
+    e = outer_degeneracy(n, g->d_off, g->d_adj, d_ord, d_pos, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(order.data(), d_ord, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        dfree(ctx, d_ord, ((size_t)n * 2 + 64) * 4, s);
+        return MCE_ECUDA;
+    }
+    // subproblem i: vertex order[i] with its neighbourhood; arena layout
+    std::vector<mce_graph> sub(n);
+    std::vector<size_t> rows_at(n), label_at(n), root_at(n);
+    size_t bytes = 0;
+    auto take = [&](size_t b) {
+        bytes = round_up(bytes, 256);
+        const size_t at = bytes;
+        bytes += b;
+        return at;
+    };
+    uint32_t max_w = 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t v = order[i], h = off[v + 1] - off[v] + 1, wl = (h + 31) / 32;
+        max_w = std::max(max_w, wl);
+        rows_at[i] = take((size_t)h * wl * 4);
+        label_at[i] = take((size_t)h * 4);
+        root_at[i] = take((size_t)2 * wl * 4);
+        sub[i].ctx = ctx;
+        sub[i].n = h;
+        sub[i].w = wl;
+        sub[i].m = (uint64_t)h * h / 4;
+        sub[i].cost_hint = (double)h * h;
+    }
+    void *arena = nullptr;
+    const size_t arena_bytes = std::max<size_t>(round_up(bytes, 256), 256);
+    rc = dalloc(ctx, &arena, arena_bytes, s);
+    if (rc != MCE_OK) {
+        dfree(ctx, d_ord, ((size_t)n * 2 + 64) * 4, s);
+        return rc;
+    }
+    unsigned char *a = static_cast<unsigned char *>(arena);
+    std::vector<mce_graph *> ptrs(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        sub[i].d_rows = reinterpret_cast<uint32_t *>(a + rows_at[i]);
+        sub[i].label = reinterpret_cast<uint32_t *>(a + label_at[i]);
+        sub[i].root = reinterpret_cast<uint32_t *>(a + root_at[i]);
+        sub[i].rv = 0;  // v's local index: set on the device by the extraction
+        ptrs[i] = &sub[i];
+    }
+    mce_batch *b = nullptr;
+    mce_options bo = o;
+    bo.flags &= ~(MCE_OUTER | MCE_AUTOTUNE | MCE_ORDER_IDENTITY);
+    if (e == cudaSuccess) rc = batch_create_impl(ctx, ptrs.data(), n, bo, std::map<uint32_t, TuneChoice>{}, &b);
+    uint64_t *d_out = nullptr;
+    const size_t obytes = MCE_OUT_WORDS(n) * 8;
+    if (e == cudaSuccess && rc == MCE_OK) rc = dalloc(ctx, (void **)&d_out, obytes, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<uint64_t> h(MCE_OUT_WORDS(n), 0);
+    if (e == cudaSuccess && rc == MCE_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+        e = outer_extract(b->d_table, n, max_w, d_ord, d_pos, g->d_off, g->d_adj, s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, obytes, s);
+        if (e == cudaSuccess) e = outer_reduce(b->d_table, n, n, d_out, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_out, obytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    float kms = 0.f;
+    if (e == cudaSuccess && rc == MCE_OK && e0 && e1) cudaEventElapsedTime(&kms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (b) mce_batch_destroy(b);
+    dfree(ctx, d_out, obytes, s);
+    dfree(ctx, arena, arena_bytes, s);
+    dfree(ctx, d_ord, ((size_t)n * 2 + 64) * 4, s);
+    if (rc == MCE_OK && e != cudaSuccess) rc = MCE_ECUDA;
+    if (rc != MCE_OK) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    rc = fill_result(h, n, res);
+    res->kernel_ms = kms;
+    res->total_ms = ms_since(t0);
+    return rc;
 }
 
 }  // namespace
@@ -1532,7 +1751,7 @@ void server_stop(mce_ctx *ctx)
 
 extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out)
 {
-    if (!ctx || !g || !out || g->ctx != ctx) return MCE_EINVAL;
+    if (!ctx || !g || !out || g->ctx != ctx || !g->d_rows) return MCE_EINVAL;
     DevicePick pick(ctx->device);
     mce_options o = defaults(opts);
     if (o.flags & (MCE_LIST | MCE_LIST_SORTED)) return MCE_ENOTIMPL;

@@ -120,7 +120,37 @@ struct BatchGraph {
     uint32_t *ren;          // n * wp renumbered words (+ pad to 16 B)
     uint64_t *out;          // MCE_OUT_WORDS(n) words
     uint32_t n, w, wp, pad;
+    // Subproblem of the outer loop (Alg. 3), else null / 0: label[i] is the
+    // original label of local vertex i (hashes and sizes use it); root holds
+    // the root's P then X as bitsets over local vertices (w words each); the
+    // root's R is {rv} (a local vertex, adjacent to every other one).
+    const uint32_t *label;
+    const uint32_t *root;
+    uint32_t rv, pad2;
 };
+
+// Outer loop of Alg. 3 (outer.cu).  CSR adjacency on the device: off[n + 1],
+// adj[off[n]] with every list sorted.
+cudaError_t outer_csr_from_edges_bytes(uint32_t n, uint64_t m, size_t *temp_bytes);
+// Builds the CSR of the simple graph given by m edges (u, v) (duplicates and
+// both orientations allowed); out[MCE_OUT_STATUS] = MCE_EINVAL on a self-loop
+// or an id >= n; *adj_count (device) receives off[n].
+cudaError_t outer_csr_from_edges(uint32_t n, uint64_t m, const uint32_t *d_uv, void *temp, size_t temp_bytes,
+                                 uint32_t *off, uint32_t *adj, uint64_t *out, cudaStream_t s);
+// CSR of an n x w bitset (off: n + 1 entries; adj: off[n] entries).
+cudaError_t outer_csr_from_rows(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t *off, uint32_t *adj,
+                                void *temp, size_t temp_bytes, size_t *need, cudaStream_t s);
+// Degeneracy order (minimum remaining degree first, smallest label on ties):
+// order[i] = vertex i, pos[v] = its position.  One block; n <= 65535 and
+// every degree < 65535.
+cudaError_t outer_degeneracy(uint32_t n, const uint32_t *off, const uint32_t *adj, uint32_t *order, uint32_t *pos,
+                             cudaStream_t s);
+// Fill every subproblem's rows, labels, root sets and table[i].rv (one block
+// each): subproblem i is vertex order[i] with its neighbourhood.
+cudaError_t outer_extract(const BatchGraph *table, uint32_t count, uint32_t max_w, const uint32_t *order,
+                          const uint32_t *pos, const uint32_t *off, const uint32_t *adj, cudaStream_t s);
+// Sum the subproblems' results into out (MCE_OUT_WORDS(n) words, zeroed).
+cudaError_t outer_reduce(const BatchGraph *table, uint32_t count, uint32_t n, uint64_t *out, cudaStream_t s);
 
 struct BatchParams {
     const BatchGraph *graphs;

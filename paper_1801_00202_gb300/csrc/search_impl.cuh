@@ -1243,8 +1243,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         // A and B every busy group has a non-empty branching set: pops and
         // queued frames always carry children, and giving work away always
         // leaves the giver at least one.
-        const bool act = work;
+        // (a frame without children would give v < 0; the group then just
+        // returns from it, reading no row)
         const int v = g.first(L);
+        const bool act = work && v >= 0;
         uint32_t Pc[K], Xc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) Pc[k] = Xc[k] = 0u;
@@ -1402,7 +1404,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (pushed && g.leader()) ++cn.don;
             if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
-        lempty = act && !desc && !more;
+        lempty = (act && !desc && !more) || (work && v < 0);
         if (desc) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -1502,51 +1504,96 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchP
         const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
         local_queue_reset(lq, bp.groups_per_block);
         const bool valid = gd.out[MCE_OUT_STATUS] == 0ull;
-        const bool root = valid && n > 0u;
+        // The root's P and X over positions: all of V and nothing, or, for a
+        // subproblem of the outer loop (Alg. 3), the given sets carried
+        // through the order, with R = {rv} already chosen.
+        const bool sub = gd.root != nullptr;
+        bool pne = false, xne = false;
+        for (uint32_t w = threadIdx.x; w < (uint32_t)WP; w += blockDim.x) {
+            uint32_t pw = 0u, xw = 0u;
+            if (!sub) {
+                const uint32_t base = w * 32u;
+                if (n >= base + 32u) pw = FULL;
+                else if (n > base) pw = (1u << (n - base)) - 1u;
+            } else {
+                for (uint32_t b = 0; b < 32u && w * 32u + b < n; ++b) {
+                    const uint32_t loc = gd.order[w * 32u + b];
+                    pw |= ((gd.root[loc >> 5] >> (loc & 31u)) & 1u) << b;
+                    xw |= ((gd.root[gd.w + (loc >> 5)] >> (loc & 31u)) & 1u) << b;
+                }
+            }
+            frames[kFrameHdr + w] = pw;
+            frames[kFrameHdr + WP + w] = xw;
+            pne = pne || pw != 0u;
+            xne = xne || xw != 0u;
+        }
+        pne = __syncthreads_or(pne) != 0;
+        xne = __syncthreads_or(xne) != 0;
+        const unsigned r0 = sub ? 1u : 0u;
+        const uint64_t s0 = sub ? mix64((uint64_t)gd.label[gd.rv] + 1u) : 0ull;
 
+        // the root is one node: internal, a leaf (R is maximal) or a dead end
         for (uint32_t j = threadIdx.x; j < MCE_OUT_WORDS(n); j += blockDim.x) {
             if (j == MCE_OUT_STATUS) continue;
             uint64_t v = 0ull;
             if (j == MCE_OUT_NODES) v = 1ull;
-            if (n > 0u && j == MCE_OUT_INTERNAL) v = 1ull;
-            if (n == 0u && (j == MCE_OUT_COUNT || j == MCE_OUT_HIST)) v = 1ull;
-            if (n == 0u && j == MCE_OUT_HASH) v = mix64(0ull ^ mix64(0ull));
+            if (pne && j == MCE_OUT_INTERNAL) v = 1ull;
+            if (!pne && xne && j == MCE_OUT_DEAD_ENDS) v = 1ull;
+            if (!pne && !xne) {
+                if (j == MCE_OUT_COUNT || j == MCE_OUT_HIST + r0) v = 1ull;
+                if (j == MCE_OUT_HASH) v = mix64(s0 ^ mix64((uint64_t)r0));
+                if (j == MCE_OUT_MAX_SIZE) v = r0;
+            }
             gd.out[j] = v;
         }
-        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) hv[j] = mix64((uint64_t)gd.order[j] + 1u);
+        for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
+            hv[j] = mix64((uint64_t)(sub ? gd.label[gd.order[j]] : gd.order[j]) + 1u);
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hk[j] = mix64((uint64_t)j);
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hist[j] = 0u;
-        for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) seq[j] = (j == 0u && root) ? 1u : j;
-        for (uint32_t w = threadIdx.x; w < (uint32_t)WP; w += blockDim.x) {
-            const uint32_t base = w * 32u;
-            uint32_t pw = 0u;
-            if (n >= base + 32u) pw = FULL;
-            else if (n > base) pw = (1u << (n - base)) - 1u;
-            frames[kFrameHdr + w] = pw;
-            frames[kFrameHdr + WP + w] = 0u;
-        }
-        if (PIVOT == MCE_PIVOT_TOMITA) {
-            if (threadIdx.x == 0) root_key = 0u;
-            __syncthreads();
+
+        // ChoosePivotOrdered at the root: the key (score + 1) << 12 | (4095 -
+        // position) is largest for the best score, earliest on ties; GreedyBB
+        // scores nothing (first of X, else of P), GreedyBBTX/NX score
+        // |P n N(u)| over X (else first of P), TomitaBB over P u X.
+        if (threadIdx.x == 0) root_key = 0u;
+        __syncthreads();
+        {
             unsigned mine = 0u;
-            for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-                unsigned deg = 0;
-                for (uint32_t w = 0; w < (uint32_t)WP; ++w) deg += __popc(gd.ren[(size_t)v * WP + w]);
-                const unsigned key = ((deg + 1u) << 12) | (4095u - v);
+            for (uint32_t u = threadIdx.x; u < n; u += blockDim.x) {
+                const bool inp = (frames[kFrameHdr + (u >> 5)] >> (u & 31u)) & 1u;
+                const bool inx = (frames[kFrameHdr + WP + (u >> 5)] >> (u & 31u)) & 1u;
+                const bool cand = (PIVOT == MCE_PIVOT_TOMITA) ? (inp || inx) : (xne ? inx : inp);
+                if (!cand) continue;
+                unsigned score = 0;
+                if (PIVOT == MCE_PIVOT_TOMITA || (PIVOT == MCE_PIVOT_GREEDY_TX && xne))
+                    for (uint32_t w = 0; w < (uint32_t)WP; ++w)
+                        score += __popc(frames[kFrameHdr + w] & gd.ren[(size_t)u * WP + w]);
+                const unsigned key = ((score + 1u) << 12) | (4095u - u);
                 mine = key > mine ? key : mine;
             }
             atomicMax(&root_key, mine);
         }
+        __syncthreads();
+        // the root frame is queued only with children to expand: with X
+        // non-empty the pivot may cover all of P (an internal node without
+        // children), and a queued frame must always carry a branching vertex
+        const unsigned p0 = root_key ? (4095u - (root_key & 4095u)) : 0u;
+        bool lne = false;
+        if (pne)
+            for (uint32_t w = threadIdx.x; w < (uint32_t)WP; w += blockDim.x)
+                lne = lne || (frames[kFrameHdr + w] & ~gd.ren[(size_t)p0 * WP + w]) != 0u;
+        lne = __syncthreads_or(lne) != 0;
+        const bool root = valid && pne && lne;
+        for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) seq[j] = (j == 0u && root) ? 1u : j;
         bool staged = true;
         if (SMEM) staged = stage_rows(srows, gd.ren, (uint32_t)rbytes, mb, phase & 1u);
         ++phase;
         __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned p0 = (PIVOT == MCE_PIVOT_TOMITA && n > 0u) ? (4095u - (root_key & 4095u)) : 0u;
             frames[0] = (p0 & 0xffffu) | (n << 16);
-            frames[1] = 0u;
-            frames[2] = 0u;
-            frames[3] = 0u;
+            frames[1] = r0;
+            frames[2] = (uint32_t)s0;
+            frames[3] = (uint32_t)(s0 >> 32);
             ctl->head = 0u;
             ctl->abort = 0u;
             ctl->tail = root ? 1u : 0u;
