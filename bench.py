@@ -172,6 +172,13 @@ def job_rate(world: int, steps: int, units_per_step: float, max_ms: float) -> fl
     return world * steps * units_per_step / (max_ms / 1e3)
 
 
+def golden_for(key):
+    p = os.path.join(ROOT, "tests", "golden", "config_results.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get(key)
+    return None
+
+
 def golden():
     p = os.path.join(ROOT, "tests", "golden", "config_results.json")
     if os.path.exists(p):
@@ -378,6 +385,49 @@ def served_form(mce, torch, ctx, specs, opts, args):
 
 # ---------------------------------------------------------------------------
 
+def other_configs():
+    """The other single-graph configurations: G(100, 0.5) seed 0, Moon-Moser
+    on 45 vertices, and the same with 5% of its edges deleted (seed 3)."""
+    return [("gnp_100_0.5_s0", 100, synth.gnp(100, 0.5, 0)),
+            ("moon_moser_45", 45, synth.moon_moser(15)),
+            ("moon_moser_45_del5", 45, synth.moon_moser_deleted(15, 0.05, 3))]
+
+
+def plain_config(mce, torch, s, dev, name, n, uv, reps, flush_l2):
+    """One graph through mce_enumerate_device on resident device input, the
+    whole path timed with events (median of `reps` after one warm-up)."""
+    opts = mce.options()
+    W = words(n)
+    rows = torch.from_numpy(synth.to_bitset(n, uv).view(np.int32).reshape(-1)).to(dev)
+    nb = mce.mce_scratch_bytes(n, opts)
+    scr = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out = torch.zeros(mce.MCE_OUT_WORDS(n), dtype=torch.int64, device=dev)
+    ms = []
+    for i in range(reps + 1):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            rc = mce.mce_enumerate_device(n, W, rows, opts, scr, nb, out, s)
+            e1.record(s)
+        if rc:
+            raise mce.MceError(rc, name)
+        torch.cuda.synchronize()
+        if i:
+            ms.append(e0.elapsed_time(e1))
+    r = mce.decode_out(out, n)
+    t = statistics.median(ms) / 1e3
+    gold = golden_for(name)
+    ops = 6 * W * r["nodes"]
+    return {"n": n, "count": r["count"], "nodes": r["nodes"], "ms": 1e3 * t,
+            "cliques_per_s": r["count"] / t, "nodes_per_s": r["nodes"] / t,
+            "alu_frac": ops / t / ALU_PEAK_OPS, "smem_frac": 8 * W * r["nodes"] / t / SMEM_PEAK_BPS,
+            "utilisation": r["busy_ns"] / max(1, r["groups"]) / (t * 1e9),
+            "donations": r["donations"], "steals": r["steals"], "global_steals": r["global_steals"],
+            "matches_oracle": bool(gold) and r["count"] == gold["count"] and r["hash"] == gold["hash"]
+                              and r["nodes"] == gold["greedy"]["nodes"] and r["status"] == 0}
+
+
 def table1_rows():
     rows = []
     for line in open(os.path.join(ROOT, "tests", "golden", "table1_random.txt")):
@@ -574,6 +624,9 @@ def run_ours(args):
     if rank != 0:
         dist.destroy_process_group()
         return 0
+    configs = {name: plain_config(mce, torch, s, dev, name, n, cuv, 5, flush_l2)
+               for name, n, cuv in other_configs()}
+
     forms = None
     if forms_in is not None:
         batch_specs, served_specs, gen = forms_in
@@ -626,6 +679,7 @@ def run_ours(args):
             "api": "mce_load_edges (pinned host edge list) + mce_enumerate + mce_graph_free"},
         "gpu_launches": 5 * args.steps + (0 if args.no_e2e else 6 * args.steps),
         "clocks": clk,
+        "other_configs": configs,
         "forms": forms,
     })
     if world == 1 and not args.no_cpu_baseline:
