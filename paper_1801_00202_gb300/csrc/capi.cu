@@ -1336,7 +1336,6 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         batch_free(b);
         return MCE_ECUDA;
     }
-    b->h_out.assign(b->out_words, 0);
     *out = b;
     return MCE_OK;
 }
@@ -1499,6 +1498,7 @@ extern "C" int mce_batch_results(mce_batch *b, mce_result *res)
 {
     if (!b) return MCE_EINVAL;
     DevicePick pick(b->ctx->device);
+    if (b->h_out.size() != b->out_words) b->h_out.assign(b->out_words, 0);  // first results call
     cudaError_t e = cudaMemcpyAsync(b->h_out.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, b->ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
     if (e != cudaSuccess) return MCE_ECUDA;
