@@ -192,6 +192,33 @@ __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned 
     return false;
 }
 
+// Take up to `want` consecutive frames (the ring's oldest) with one ticket
+// advance: consumer tickets first .. first + k - 1.  Returns k (0 when the
+// ring is empty or the tries ran out).
+__device__ __forceinline__ unsigned q_reserve_pop_many(Ctl *ctl, unsigned *seq, unsigned mask, unsigned want,
+                                                       unsigned &first, uint64_t &fails, unsigned tries)
+{
+    unsigned pos = ld_relaxed(&ctl->head);
+    for (unsigned t = 0; t < tries; ++t) {
+        unsigned k = 0;
+        while (k < want && ld_acquire(&seq[(pos + k) & mask]) == pos + k + 1u) ++k;
+        if (k == 0) {
+            const int dif = (int)(ld_acquire(&seq[pos & mask]) - (pos + 1));
+            if (dif < 0) return 0u;  // empty
+            pos = ld_relaxed(&ctl->head);
+            continue;
+        }
+        const unsigned prev = atomicCAS(&ctl->head, pos, pos + k);
+        if (prev == pos) {
+            first = pos;
+            return k;
+        }
+        ++fails;
+        pos = prev;
+    }
+    return 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Group-wide set primitives.  All collectives use the full warp mask and must
 // be reached by all 32 lanes: call them only as standalone statements in
@@ -1162,13 +1189,32 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             // through the block ring).
             // (A block-private ring, as in the batched form, has no other
             // contenders: there every idle group asks.)
+            // The polling warp's first asking group takes frames for up to four
+            // of the warp's asking groups with one ticket advance.
             unsigned ticket = 0, got = 0;
             const bool ring_shared = prm.total_groups > (blockDim.x >> 5) * (32u / G);
             const bool ask = !work && queued != 0u && lt == lh && (poller || !ring_shared) && g.leader();
             const unsigned askers = __ballot_sync(FULL, ask);
-            if (ask && (!ring_shared || g.lane == (unsigned)(__ffs(askers) - 1))) {
-                ++cn.gtry;
-                got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.cas_fail, prm.tune.pop_tries) ? 1u : 0u;
+            if (!ring_shared) {
+                if (ask) {
+                    ++cn.gtry;
+                    got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.cas_fail, prm.tune.pop_tries) ? 1u : 0u;
+                }
+            } else if (askers != 0u) {
+                const unsigned lead = (unsigned)(__ffs(askers) - 1);
+                unsigned first = 0u, k = 0u;
+                if (g.lane == lead) {
+                    ++cn.gtry;
+                    k = q_reserve_pop_many(ctl, prm.seq, qmask, min(4u, (unsigned)__popc(askers)), first,
+                                           cn.cas_fail, prm.tune.pop_tries);
+                }
+                k = __shfl_sync(FULL, k, (int)lead);
+                first = __shfl_sync(FULL, first, (int)lead);
+                const unsigned rank = (unsigned)__popc(askers & ((1u << g.lane) - 1u));
+                if (ask && rank < k) {
+                    got = 1u;
+                    ticket = first + rank;
+                }
             }
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
