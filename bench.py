@@ -105,8 +105,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"mce_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -217,9 +217,19 @@ def _gen_served(r: int):
     return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
 
 
+def _oracle_batch_graph(i: int):
+    import oracle
+    g = synth.batch_graph(i)
+    t = time.perf_counter()
+    r = oracle.tomita(g.n, g.uv)
+    return r["count"], time.perf_counter() - t
+
+
 def generate_forms(args):
     """Build the batched and served graphs on all host cores (spawned pool,
-    before any CUDA call); bitset rows come back."""
+    before any CUDA call); bitset rows come back.  The same pool then times
+    the CPU oracle, one graph per core, on an evenly spaced sample of the
+    batched workload (its all-cores baseline)."""
     import multiprocessing as mp
     total = args.served_warmup + args.served_requests
     cores = max(1, min(os.cpu_count() or 1, 32))
@@ -227,7 +237,23 @@ def generate_forms(args):
     with mp.get_context("spawn").Pool(cores) as pool:
         batch = pool.map(_gen_batch, range(args.batch_graphs), chunksize=32)
         served = pool.map(_gen_served, range(total), chunksize=64)
-    return batch, served, {"cores": cores, "seconds": time.perf_counter() - t}
+        gen_s = time.perf_counter() - t
+        base = None
+        if args.oracle_sample and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            step = max(1, args.batch_graphs // args.oracle_sample)
+            sample = list(range(0, args.batch_graphs, step))[:args.oracle_sample]
+            t = time.perf_counter()
+            res = pool.map(_oracle_batch_graph, sample, chunksize=1)
+            wall = time.perf_counter() - t
+            cliques = sum(c for c, _ in res)
+            base = {"value": len(sample) / wall, "unit": "graphs/s", "cores": cores, "kind": "oracle",
+                    "cliques_per_s": cliques / wall,
+                    "sample": f"Bron-Kerbosch with the Tomita pivot, one graph per host core, on every "
+                              f"{step}th graph of the batched workload ({len(sample)} graphs, "
+                              f"{cliques} maximal cliques, {wall:.1f} s)"}
+    return batch, served, {"cores": cores, "seconds": gen_s}, base
 
 
 def _work(results, ns):
@@ -428,6 +454,33 @@ def plain_config(mce, torch, s, dev, name, n, uv, reps, flush_l2):
                               and r["nodes"] == gold["greedy"]["nodes"] and r["status"] == 0}
 
 
+def listing_runs(mce, torch, device, stream, uv):
+    """The listing through mce_enumerate on the measured graph: every maximal
+    clique returned to host buffers (CSR), unsorted and in lexicographic
+    order; wall time of the call (search, record chunks -> CSR on the
+    device, copy to the host)."""
+    gold = golden() or {}
+    need_ids = sum(int(k) * c for k, c in gold.get("hist", {}).items())
+    if not need_ids:
+        return None
+    ctx = mce.Context(device, stream=stream)
+    g = ctx.load_edges(N, uv)
+    out = {}
+    for name, flags in (("unsorted", mce.MCE_LIST), ("sorted", mce.MCE_LIST_SORTED)):
+        o = mce.options(flags=flags)
+        g.enumerate(o, list_cap=need_ids, off_cap=gold["count"] + 1)   # warm
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = g.enumerate(o, list_cap=need_ids, off_cap=gold["count"] + 1)
+        sec = time.perf_counter() - t
+        out[name] = {"ms": 1e3 * sec, "cliques_per_s": r["count"] / sec, "ids": int(r["list_off"][-1]),
+                     "host_bytes": int(r["list_off"][-1]) * 4 + (r["count"] + 1) * 8,
+                     "matches_oracle": r["count"] == gold["count"] and r["hash"] == gold["hash"]}
+    g.free()
+    ctx.close()
+    return out
+
+
 def table1_rows():
     rows = []
     for line in open(os.path.join(ROOT, "tests", "golden", "table1_random.txt")):
@@ -626,14 +679,16 @@ def run_ours(args):
         return 0
     configs = {name: plain_config(mce, torch, s, dev, name, n, cuv, 5, flush_l2)
                for name, n, cuv in other_configs()}
+    listing = listing_runs(mce, torch, local, s, uv)
 
     forms = None
     if forms_in is not None:
-        batch_specs, served_specs, gen = forms_in
+        batch_specs, served_specs, gen, batch_base = forms_in
         fctx = mce.Context(local, stream=s)
         fclk = ClockSampler(local)
         fclk.start()
         forms = {"batched": batched_form(mce, torch, fctx, s, batch_specs, mce.options(), args, flush_l2)}
+        forms["batched"]["cpu_oracle_all_cores"] = batch_base
         forms["served"] = served_form(mce, torch, fctx, served_specs, mce.options(), args)
         forms["clocks"] = fclk.stop()
         forms["generation"] = gen
@@ -680,6 +735,7 @@ def run_ours(args):
         "gpu_launches": 5 * args.steps + (0 if args.no_e2e else 6 * args.steps),
         "clocks": clk,
         "other_configs": configs,
+        "listing": listing,
         "forms": forms,
     })
     if world == 1 and not args.no_cpu_baseline:
@@ -708,6 +764,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--served-warmup", type=int, default=2000)
+    ap.add_argument("--oracle-sample", type=int, default=256,
+                    help="batched graphs the CPU oracle runs on all host cores (0: skip)")
     ap.add_argument("--plain-sample", type=int, default=4000,
                     help="served requests also run through the plain form for the comparison")
     # launch-shape overrides (0 = the library's choice)
