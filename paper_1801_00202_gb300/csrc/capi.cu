@@ -929,6 +929,7 @@ struct mce_batch {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     std::vector<mce_batch_bucket> info;  // launch choice of every bucket
     const BatchGraph *d_table = nullptr;
+    cudaStream_t stream = nullptr;       // where it is planned and launched
 };
 
 namespace {
@@ -974,8 +975,8 @@ void batch_free(mce_batch *b)
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
-    if (b->dmem) dfree(b->ctx, b->dmem, b->dbytes);
-    cudaStreamSynchronize(b->ctx->stream);
+    if (b->dmem) dfree(b->ctx, b->dmem, b->dbytes, b->stream);
+    cudaStreamSynchronize(b->stream);
     delete b;
 }
 
@@ -1004,7 +1005,8 @@ TuneChoice default_choice(uint32_t n, const mce_options &o)
 // Plan and capture a batch with the launch choice of every words class
 // given in `choice` (classes not in it: the defaults).
 int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
-                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out);
+                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out,
+                      cudaStream_t stream = nullptr);
 
 // Milliseconds of one launch of a batch planned with `choice` (the second of
 // two launches), or a negative value if it cannot run.
@@ -1125,7 +1127,7 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
 namespace {
 
 int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
-                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out)
+                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out, cudaStream_t stream)
 {
     *out = nullptr;
     int dev = 0, sms = 0, optin = 0;
@@ -1137,6 +1139,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
     mce_batch *b = new (std::nothrow) mce_batch;
     if (!b) return MCE_ENOMEM;
     b->ctx = ctx;
+    b->stream = stream ? stream : ctx->stream;
     b->count = count;
     b->n.resize(count);
 
@@ -1244,7 +1247,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         b->info.push_back(bi);
     }
     b->dbytes = round_up(off, 256);
-    rc = dalloc(ctx, &b->dmem, b->dbytes);
+    rc = dalloc(ctx, &b->dmem, b->dbytes, b->stream);
     if (rc != MCE_OK) { delete b; return rc; }
     unsigned char *base = static_cast<unsigned char *>(b->dmem);
     b->d_out = reinterpret_cast<uint64_t *>(base + out_at);
@@ -1266,7 +1269,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         t.rv = graphs[i]->rv;
         t.pad2 = 0;
     }
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = b->stream;
     cudaError_t e = cudaSuccess;
     if (count) e = cudaMemcpyAsync(base + table_off, table.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s);
     for (const Bucket &bk : buckets)
@@ -1488,9 +1491,9 @@ extern "C" int mce_batch_launch(mce_batch *b)
 {
     if (!b) return MCE_EINVAL;
     DevicePick pick(b->ctx->device);
-    cudaError_t e = cudaEventRecord(b->t0, b->ctx->stream);
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->ctx->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->ctx->stream);
+    cudaError_t e = cudaEventRecord(b->t0, b->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
     return cuda_code(e);
 }
 
@@ -1499,8 +1502,8 @@ extern "C" int mce_batch_results(mce_batch *b, mce_result *res)
     if (!b) return MCE_EINVAL;
     DevicePick pick(b->ctx->device);
     if (b->h_out.size() != b->out_words) b->h_out.assign(b->out_words, 0);  // first results call
-    cudaError_t e = cudaMemcpyAsync(b->h_out.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, b->ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(b->h_out.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return MCE_ECUDA;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->t0, b->t1);
@@ -1558,11 +1561,21 @@ namespace {
 
 constexpr int kServeSlots = 128;
 constexpr size_t kServeStackBytes = 56 * 1024;  // shared-memory stack per block
+// Micro-batches: while at least kBatchMin requests that can share a launch
+// wait, up to kBatchMax of them (each expecting at most kBatchCost maximal
+// cliques) run as one batched launch on one stream slot.
+constexpr size_t kBatchMin = 4, kBatchMax = 256;
+constexpr double kBatchCost = 1e5;
+
+struct MicroBatch;
 
 struct Request {
     mce_ticket id = 0;
     mce_graph *g = nullptr;
     mce_options o{};
+    bool batchable = false;  // default launch options and a small expected cost
+    MicroBatch *mb = nullptr;
+    uint32_t mb_index = 0;
     Config c;
     Layout L;
     uint64_t scratch_bytes = 0, out_bytes = 0, need = 0;
@@ -1576,6 +1589,12 @@ struct Request {
     float kernel_ms = 0.f;
 };
 
+struct MicroBatch {
+    mce_batch *b = nullptr;
+    int slot = -1;
+    std::vector<Request *> reqs;
+};
+
 }  // namespace
 
 struct Server {
@@ -1584,6 +1603,7 @@ struct Server {
     std::condition_variable cv, done_cv;
     std::deque<Request *> pending;
     std::vector<Request *> running;
+    std::vector<MicroBatch *> batches;  // micro-batches on the device
     std::unordered_map<mce_ticket, Request *> all;
     std::thread th;
     bool stop = false;
@@ -1654,6 +1674,91 @@ bool admit(Server *sv, Request *r)
     return true;
 }
 
+// Run batchable requests with the pivot rule of the front one, gathered in
+// arrival order from the first kBatchScan queued, as one batched launch on a
+// free slot; false when none was formed.
+constexpr size_t kBatchScan = 4096;
+
+bool admit_batch(Server *sv)
+{
+    const uint32_t pivot = sv->pending.front()->o.pivot_mode;
+    std::vector<size_t> pick;
+    for (size_t i = 0; i < sv->pending.size() && i < kBatchScan && pick.size() < kBatchMax; ++i)
+        if (sv->pending[i]->batchable && sv->pending[i]->o.pivot_mode == pivot) pick.push_back(i);
+    const size_t k = pick.size();
+    if (k < kBatchMin) return false;
+    int slot = -1;
+    for (int i = 0; i < kServeSlots; ++i)
+        if (!sv->busy[i]) { slot = i; break; }
+    if (slot < 0) return false;
+    std::vector<mce_graph *> graphs(k);
+    for (size_t i = 0; i < k; ++i) graphs[i] = sv->pending[pick[i]]->g;
+    mce_options o{};
+    o.pivot_mode = pivot;
+    mce_batch *b = nullptr;
+    if (batch_create_impl(sv->ctx, graphs.data(), (uint32_t)k, o, std::map<uint32_t, TuneChoice>{}, &b,
+                          sv->streams[slot]) != MCE_OK)
+        return false;  // e.g. memory: the requests go one by one
+    cudaStream_t s = sv->streams[slot];
+    cudaError_t e = cudaEventRecord(sv->ev0[slot], s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sv->ev1[slot], s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        mce_batch_destroy(b);
+        return false;
+    }
+    MicroBatch *mb = new MicroBatch;
+    mb->b = b;
+    mb->slot = slot;
+    sv->busy[slot] = true;
+    std::vector<Request *> taken(k);
+    for (size_t i = 0; i < k; ++i) taken[i] = sv->pending[pick[i]];
+    for (size_t i = k; i-- > 0;) sv->pending.erase(sv->pending.begin() + (long)pick[i]);
+    for (size_t i = 0; i < k; ++i) {
+        Request *r = taken[i];
+        r->mb = mb;
+        r->mb_index = (uint32_t)i;
+        r->slot = slot;
+        r->state = 1;
+        mb->reqs.push_back(r);
+    }
+    sv->batches.push_back(mb);
+    return true;
+}
+
+// A finished micro-batch: results to its requests, launch resources freed.
+void retire_batch(Server *sv, MicroBatch *mb, bool ok)
+{
+    mce_batch *b = mb->b;
+    std::vector<uint64_t> h;
+    float ms = 0.f;
+    if (ok) {
+        h.resize(b->out_words);
+        ok = cudaMemcpy(h.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+        cudaEventElapsedTime(&ms, sv->ev0[mb->slot], sv->ev1[mb->slot]);
+    }
+    const auto now = std::chrono::steady_clock::now();
+    for (Request *r : mb->reqs) {
+        if (ok) {
+            const size_t at = b->out_off[r->mb_index];
+            r->words.assign(h.begin() + (long)at, h.begin() + (long)(at + MCE_OUT_WORDS(r->g->n)));
+            r->rc = (int)(int64_t)r->words[MCE_OUT_STATUS];
+            if (r->rc > 0) r->rc = MCE_OK;
+            r->kernel_ms = ms;
+        } else {
+            r->rc = MCE_ECUDA;
+        }
+        r->mb = nullptr;
+        r->slot = -1;
+        r->state = 2;
+        r->t_done = now;
+    }
+    sv->busy[mb->slot] = false;
+    mce_batch_destroy(b);
+    delete mb;
+}
+
 void serve_loop(Server *sv)
 {
     DevicePick pick(sv->ctx->device);
@@ -1669,6 +1774,15 @@ void serve_loop(Server *sv)
             sv->running.pop_back();
             changed = true;
         }
+        for (size_t k = 0; k < sv->batches.size();) {
+            MicroBatch *mb = sv->batches[k];
+            const cudaError_t q = cudaEventQuery(sv->ev1[mb->slot]);
+            if (q == cudaErrorNotReady) { ++k; continue; }
+            retire_batch(sv, mb, q == cudaSuccess);
+            sv->batches[k] = sv->batches.back();
+            sv->batches.pop_back();
+            changed = true;
+        }
         while (!sv->pending.empty()) {
             Request *r = sv->pending.front();
             if (r->need > sv->ctx->budget && sv->ctx->budget) {  // can never fit
@@ -1679,12 +1793,16 @@ void serve_loop(Server *sv)
                 changed = true;
                 continue;
             }
+            if (sv->pending.size() >= kBatchMin && admit_batch(sv)) {
+                changed = true;
+                continue;
+            }
             if (!admit(sv, r)) break;
             sv->pending.pop_front();
             changed = true;
         }
         if (changed) sv->done_cv.notify_all();
-        if (sv->running.empty() && sv->pending.empty()) {
+        if (sv->running.empty() && sv->batches.empty() && sv->pending.empty()) {
             sv->cv.wait(lk);
         } else {
             lk.unlock();
@@ -1738,6 +1856,8 @@ void server_stop(mce_ctx *ctx)
     sv->th.join();
     for (int i = 0; i < kServeSlots; ++i) cudaStreamSynchronize(sv->streams[i]);
     for (Request *r : sv->running) retire(sv, r, MCE_ECUDA);
+    for (MicroBatch *mb : sv->batches) retire_batch(sv, mb, false);
+    sv->batches.clear();
     for (auto &kv : sv->all) delete kv.second;
     for (int i = 0; i < kServeSlots; ++i) {
         cudaStreamDestroy(sv->streams[i]);
@@ -1760,9 +1880,13 @@ extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, m
         if (rc) return rc;
     }
     Server *sv = ctx->server;
+    const double cost = expected_cliques(g->n, g->m);
+    // default launch options and a small expected cost: may share a launch
+    const bool batchable = !o.lanes_per_subtree && !o.words_per_lane && !o.threads_per_block && !o.blocks &&
+                           !o.split_min_p && !o.stack_levels && !o.queue_log2 && !o.flags && !o.timeout_ns &&
+                           cost <= kBatchCost;
     if (!o.threads_per_block) o.threads_per_block = 256;
     if (!o.blocks) {
-        const double cost = expected_cliques(g->n, g->m);
         const double per_block = default_tuning().serve_cpb;
         o.blocks = (uint32_t)std::min<double>(std::max(1.0, std::ceil(cost / per_block)), 4.0 * sv->sms);
     }
@@ -1770,6 +1894,7 @@ extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, m
     if (!r) return MCE_ENOMEM;
     r->g = g;
     r->o = o;
+    r->batchable = batchable;
     int rc = g->n > MCE_NMAX ? MCE_EINVAL : choose(g->n, o, r->c, kServeStackBytes);
     if (rc) { delete r; return rc; }
     r->L = layout(g->n, r->c);

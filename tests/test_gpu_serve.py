@@ -68,3 +68,28 @@ def test_wait_and_small_budget(mce):
     for g in graphs:
         g.free()
     ctx.close()
+
+
+@pytest.mark.parametrize("pivot", ["greedy", "tomita"])
+def test_queued_requests_share_launches(mce, pivot):
+    # many small requests submitted at once queue up and run as batched
+    # launches (the scheduler's micro-batches); each result is its own
+    ctx = mce.Context(0)
+    specs = [(n, synth.gnp(n, p, 500 + i)) for i, (n, p) in
+             enumerate([(40, 0.5), (90, 0.4), (150, 0.3), (33, 0.7), (250, 0.15), (64, 0.5)] * 12)]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    opts = mce.options(pivot=pivot)
+    alone = [g.enumerate(opts) for g in graphs]
+    tickets = [ctx.submit(g, None if pivot == "greedy" else opts) for g in graphs]
+    got = [ctx.wait(t, timeout_ns=60_000_000_000) for t in tickets]
+    for a, r in zip(alone, got):
+        assert r["rc"] == 0
+        assert (r["count"], r["hash"], r["nodes"], r["internal"], r["dead_ends"]) == \
+            (a["count"], a["hash"], a["nodes"], a["internal"], a["dead_ends"])
+        assert np.array_equal(r["hist"], a["hist"])
+    for (n, uv), r in list(zip(specs, got))[:6]:
+        ref = oracle.tomita(n, uv)
+        assert (r["count"], r["hash"]) == (ref["count"], ref["hash"])
+    for g in graphs:
+        g.free()
+    ctx.close()
