@@ -201,6 +201,15 @@ Layout layout(uint32_t n, const Config &c)
     return L;
 }
 
+// Smallest power of two >= v (v >= 1), capped at 2^31: the kernel tests the
+// check periods with a mask.
+uint32_t pow2_ceil(uint32_t v)
+{
+    uint32_t p = 1u;
+    while (p < v && p < 0x80000000u) p <<= 1;
+    return p;
+}
+
 int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErrorMemoryAllocation ? MCE_ENOMEM : MCE_ECUDA); }
 
 }  // namespace
@@ -218,8 +227,8 @@ Tuning mce::default_tuning()
                 if (std::sscanf(p, "%31[a-z_]=%u%n", key, &val, &used) != 2) break;
                 if (!std::strcmp(key, "share_local")) d.share_local = val;
                 else if (!std::strcmp(key, "share_global")) d.share_global = val;
-                else if (!std::strcmp(key, "local_check") && val) d.local_check = val;
-                else if (!std::strcmp(key, "global_check") && val) d.global_check = val;
+                else if (!std::strcmp(key, "local_check") && val) d.local_check = pow2_ceil(val);
+                else if (!std::strcmp(key, "global_check") && val) d.global_check = pow2_ceil(val);
                 else if (!std::strcmp(key, "refresh_ns")) d.refresh_ns = val;
                 else if (!std::strcmp(key, "serve_cpb") && val) d.serve_cpb = val;
                 else if (!std::strcmp(key, "pop_tries") && val) d.pop_tries = val;

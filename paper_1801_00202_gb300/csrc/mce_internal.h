@@ -79,8 +79,8 @@ struct ListParams {
 struct Tuning {
     uint32_t share_local;   // smallest |P| given to the block ring (0: by density)
     uint32_t share_global;  // smallest |P| given to the device-wide ring (0: by density)
-    uint32_t local_check;   // busy warps: iterations between block-ring checks
-    uint32_t global_check;  // busy warps: iterations between global checks
+    uint32_t local_check;   // busy warps: iterations between block-ring checks (a power of two)
+    uint32_t global_check;  // busy warps: iterations between global checks (a power of two)
     uint32_t refresh_ns;    // age of a block's cached view of the global ring
     uint32_t serve_cpb;     // served form: expected maximal cliques per block
     uint32_t pop_tries;     // ticket attempts of one take from the device-wide ring

@@ -1057,7 +1057,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 
         // ---- B1: the block ring (idle groups take, busy groups refill)
         const unsigned busy_b = __ballot_sync(FULL, work);
-        if (busy_b != FULL || (it % prm.tune.local_check) == 0u) {
+        if (busy_b != FULL || (it & (prm.tune.local_check - 1u)) == 0u) {
             unsigned lh = 0, lt = 0, li = 0, ld = 0;
             if (g.lane == 0) {
                 lh = vld(&lq.h->head);
@@ -1113,7 +1113,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         // read by the block's polling warp (an all-idle warp) or, at most
         // every tune.refresh_ns, by one busy warp, and cached in shared memory.
         const unsigned busy2 = __ballot_sync(FULL, work);
-        if (busy2 == 0u || (it % prm.tune.global_check) == 0u) {
+        if (busy2 == 0u || (it & (prm.tune.global_check - 1u)) == 0u) {
             unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
             bool pol = poller;
             if (g.lane == 0) {
