@@ -128,7 +128,8 @@ typedef struct {
     uint32_t words_per_lane;    /* 32-bit words of each set a lane holds:
                                    1,2,4; 0 = autotuned                       */
     uint32_t blocks;            /* persistent grid size; 0 = one wave         */
-    uint32_t threads_per_block; /* 0 = autotuned                              */
+    uint32_t threads_per_block; /* 0 = autotuned; a multiple of 32, at most
+                                   512 (else MCE_EINVAL)                      */
     uint64_t timeout_ns;        /* device-side wait budget: a search whose
                                    idle warps see no progress for this long
                                    stops with MCE_ETIMEOUT; 0 = 60 s          */

@@ -110,9 +110,8 @@ void default_shape(uint32_t n, int &G, int &K)
     else { G = 32; K = 4; }
 }
 
-// Shape for n vertices under the caller's options: forced lanes/words win;
-// otherwise the default, narrowed to two words per lane when the caller asks
-// for more threads per block than four-word shapes allow.
+// Shape for n vertices under the caller's options: forced lanes/words win,
+// otherwise the default.
 void pick_shape(uint32_t n, const mce_options &o, int &G, int &K)
 {
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
@@ -122,17 +121,18 @@ void pick_shape(uint32_t n, const mce_options &o, int &G, int &K)
         if (o.words_per_lane) K = (int)o.words_per_lane;
         else K = (int)std::max<uint32_t>(1, (W + G - 1) / G);
         if (K == 3) K = 4;
-    } else if (o.threads_per_block > 512u && K == 4 && G < 32) {
-        K = 2;
-        G *= 2;
     }
 }
 
-unsigned default_threads(uint32_t n, int K)
+// The search kernels are built for at most kMaxThreads threads per block
+// (128 registers per thread: the group state of four-word lanes, and no
+// spills for the narrower shapes).
+constexpr unsigned kMaxThreads = 512u;
+
+unsigned default_threads(uint32_t n)
 {
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
-    if (W <= 4) return 256u;
-    return K >= 4 ? 512u : 1024u;
+    return W <= 4 ? 256u : kMaxThreads;
 }
 
 // stack_cap: most shared memory for the explicit stack per block (the served
@@ -163,8 +163,8 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode, c.list);
     if (search_smem(n, c.wp, c.smem, c.list) > limit) return MCE_EINVAL;
 
-    c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n, K);
-    if (c.threads % 32 || c.threads > (K >= 4 ? 512u : 1024u)) return MCE_EINVAL;
+    c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n);
+    if (c.threads % 32 || c.threads > kMaxThreads) return MCE_EINVAL;
     const size_t base = search_smem(n, c.wp, c.smem, c.list);
     const size_t cap = stack_cap < limit - base ? base + stack_cap : limit;
     plan_stack_for((uint32_t)base, c.G, c.K, c.threads, cap, c.stack_levels, c.stack_offset, c.smem_bytes);
@@ -1222,7 +1222,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         size_t base = 0;
         for (uint32_t i : bk.graphs) base = std::max(base, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
         const unsigned threads = bk.threads;
-        if (threads % 32 || threads > (bk.K >= 4 ? 512u : 1024u)) { rc = MCE_EINVAL; break; }
+        if (threads % 32 || threads > kMaxThreads) { rc = MCE_EINVAL; break; }
         // at most 56 KB of stack per block, so that several blocks share an SM
         size_t smem = 0;
         plan_stack_for((uint32_t)base, bk.G, bk.K, threads, std::min<size_t>(slimit, base + 56 * 1024),

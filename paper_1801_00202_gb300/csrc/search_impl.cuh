@@ -267,6 +267,40 @@ struct Grp {
         int r = __shfl_sync(FULL, loc, src);
         return b ? r : -1;
     }
+    // Emptiness of sets a and b, and the first element of a when a is
+    // non-empty, else of b (-1 when both are empty).
+    __device__ __forceinline__ int first_either(const uint32_t (&a)[K], const uint32_t (&b)[K], bool &na,
+                                                bool &nb) const
+    {
+        uint32_t oa = 0, ob = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            oa |= a[k];
+            ob |= b[k];
+        }
+        unsigned ba = 0u, bb = 0u;
+        if (G == 1) {
+            na = oa != 0u;
+            nb = ob != 0u;
+        } else {
+            ba = __ballot_sync(FULL, oa != 0u) & gmask;
+            bb = __ballot_sync(FULL, ob != 0u) & gmask;
+            na = ba != 0u;
+            nb = bb != 0u;
+        }
+        int loc = -1;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const uint32_t w = na ? a[k] : b[k];
+            if (w) loc = (int)((gl * K + k) * 32u) + __ffs(w) - 1;
+        }
+        if (G == 1) return loc;
+        if (G == 32) return (int)__reduce_min_sync(FULL, (unsigned)loc);
+        const unsigned m = na ? ba : bb;
+        const int src = m ? (__ffs(m) - 1) : (int)lane;
+        const int r = __shfl_sync(FULL, loc, src);
+        return m ? r : -1;
+    }
     // Emptiness of two sets at once.
     __device__ __forceinline__ void any2(const uint32_t (&a)[K], const uint32_t (&b)[K], bool &ra, bool &rb) const
     {
@@ -436,7 +470,8 @@ __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned grou
     }
 }
 
-// Per-warp result counters (meaningful in group leaders; summed at the end).
+// Per-warp result counters (meaningful in group leaders; summed at the end;
+// nodes is formed at the flush as leaves + dead ends + internal nodes).
 struct Counters {
     uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0, gsteals = 0, busy = 0;
     uint64_t gpush = 0, gtry = 0, cas_fail = 0;  // device-wide ring diagnostics
@@ -571,6 +606,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
 // warp).  Called by all 32 lanes.
 __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
 {
+    c.nodes = c.cnt + c.dead + c.intl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         c.cnt += __shfl_xor_sync(FULL, c.cnt, o);
@@ -673,7 +709,8 @@ template <int G, int K>
 struct Stack {
     static constexpr int M = (G >= 4) ? 1 : 4;
     static constexpr int LW = 2 * K + M;
-    uint32_t *sm;  // this lane's column of the warp's slice (kept in a register)
+    uint32_t *sm;  // the warp's slice of shared memory (kept in a register)
+    unsigned ln;   // this lane
     int SL;
     uint32_t (*lw)[LW];  // local-memory levels, indexed by the absolute level
 
@@ -681,21 +718,48 @@ struct Stack {
     {
         return j == 0u ? pe : (j == 1u ? rs : (j == 2u ? (uint32_t)S : (uint32_t)(S >> 32)));
     }
+    // A shared-memory level: P of all 32 lanes (K words each, lane-major, so
+    // one vector access per lane), then X likewise, then M meta words per
+    // lane (word-major).  The region starts 16-byte aligned and a level is
+    // 128 * LW bytes, so every vector is aligned.
+    __device__ __forceinline__ static void st_vec(uint32_t *p, const uint32_t (&v)[K])
+    {
+        if (K == 1) {
+            p[0] = v[0];
+        } else if (K == 2) {
+            *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+        } else {
+            *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+        }
+    }
+    __device__ __forceinline__ static void ld_vec(const uint32_t *p, uint32_t (&v)[K])
+    {
+        if (K == 1) {
+            v[0] = p[0];
+        } else if (K == 2) {
+            const uint2 t = *reinterpret_cast<const uint2 *>(p);
+            v[0] = t.x;
+            v[1] = t.y;
+        } else {
+            const uint4 t = *reinterpret_cast<const uint4 *>(p);
+            v[0] = t.x;
+            v[1] = t.y;
+            v[2] = t.z;
+            v[3] = t.w;
+        }
+    }
     __device__ __forceinline__ void put(int d, unsigned gl, const uint32_t (&P)[K], const uint32_t (&X)[K],
                                         unsigned pe, unsigned rs, uint64_t S)
     {
         if (d < SL) {
             uint32_t *w = sm + (size_t)d * LW * 32;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                w[k * 32] = P[k];
-                w[(K + k) * 32] = X[k];
-            }
+            st_vec(w + ln * K, P);
+            st_vec(w + 32 * K + ln * K, X);
             if (M == 1) {
-                if (gl < 4u) w[2 * K * 32] = pick(pe, rs, S, gl);
+                if (gl < 4u) w[2 * K * 32 + ln] = pick(pe, rs, S, gl);
             } else {
 #pragma unroll
-                for (int j = 0; j < M; ++j) w[(2 * K + j) * 32] = pick(pe, rs, S, (unsigned)j);
+                for (int j = 0; j < M; ++j) w[(2 * K + j) * 32 + ln] = pick(pe, rs, S, (unsigned)j);
             }
         } else {
 #pragma unroll
@@ -715,11 +779,8 @@ struct Stack {
     {
         if (d < SL) {
             uint32_t *w = sm + (size_t)d * LW * 32;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                w[k * 32] = P[k];
-                w[(K + k) * 32] = X[k];
-            }
+            st_vec(w + ln * K, P);
+            st_vec(w + 32 * K + ln * K, X);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -732,13 +793,10 @@ struct Stack {
     {
         if (d < SL) {
             const uint32_t *w = sm + (size_t)d * LW * 32;
+            ld_vec(w + ln * K, P);
+            ld_vec(w + 32 * K + ln * K, X);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                P[k] = w[k * 32];
-                X[k] = w[(K + k) * 32];
-            }
-#pragma unroll
-            for (int j = 0; j < M; ++j) mr[j] = w[(2 * K + j) * 32];
+            for (int j = 0; j < M; ++j) mr[j] = w[(2 * K + j) * 32 + ln];
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -851,7 +909,8 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     uint32_t stack_local[kStackDepth][Stk::LW];
     Stk stk;
     stk.SL = stack_smem_levels;
-    stk.sm = stack_smem + (size_t)(threadIdx.x >> 5) * (size_t)stack_smem_levels * Stk::LW * 32 + g.lane;
+    stk.sm = stack_smem + (size_t)(threadIdx.x >> 5) * (size_t)stack_smem_levels * Stk::LW * 32;
+    stk.ln = g.lane;
     stk.lw = stack_local;
 
     uint64_t quiet_since = 0;
@@ -1310,28 +1369,31 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         }
         // first vertices of X' and P' (ChoosePivotOrdered's candidates) also
         // answer the emptiness tests of the leaf test
-        const int fx = g.first(Xc);
-        const int fp = g.first(Pc);
-        const bool bx = fx >= 0, bp = fp >= 0;
+        bool bx, bp;
+        int fp = -1, pg = -1;
+        if (PIVOT == MCE_PIVOT_GREEDY) {
+            pg = g.first_either(Xc, Pc, bx, bp);
+        } else {
+            const int fx = g.first(Xc);
+            fp = g.first(Pc);
+            bx = fx >= 0;
+            bp = fp >= 0;
+        }
         uint64_t Sc = 0;
         if (act) Sc = S + hv[v];  // every lane keeps |R| and S
-        if (act && g.leader()) {
-            ++cn.nodes;
-            if (!bp) {
-                if (!bx) {  // P u X empty: R u {v} is a maximal clique
-                    const unsigned k = rs + 1u;
-                    ++cn.cnt;
-                    cn.hash += mix64(Sc ^ hk[k]);
-                    cn.max = k > cn.max ? k : cn.max;
-                    const unsigned old = atomicAdd(&hist[k], 1u);
-                    if (old == 0xffffffffu)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(prm.out + MCE_OUT_HIST + k), 1ull << 32);
-                } else {
-                    ++cn.dead;
-                }
-            } else {
-                ++cn.intl;
-            }
+        // every node is internal, a leaf or a dead end (nodes = their sum,
+        // formed when the counters are flushed)
+        const bool lead = act && g.leader();
+        cn.intl += (lead && bp) ? 1u : 0u;
+        cn.dead += (lead && !bp && bx) ? 1u : 0u;
+        if (lead && !bp && !bx) {  // P u X empty: R u {v} is a maximal clique
+            const unsigned k = rs + 1u;
+            ++cn.cnt;
+            cn.hash += mix64(Sc ^ hk[k]);
+            cn.max = k > cn.max ? k : cn.max;
+            const unsigned old = atomicAdd(&hist[k], 1u);
+            if (old == 0xffffffffu)
+                atomicAdd(reinterpret_cast<unsigned long long *>(prm.out + MCE_OUT_HIST + k), 1ull << 32);
         }
         if (list) {
             const bool emit = act && !bp && !bx;
@@ -1342,7 +1404,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         // ChoosePivotOrdered on the child (P', X')
         int pc;
         if (PIVOT == MCE_PIVOT_GREEDY) {
-            pc = bx ? fx : fp;
+            pc = pg;
         } else {
             // argmax |P' n N(u)| over X' (TX) or P' u X' (TomitaBB); scanning
             // candidates in increasing position with '>' keeps the earliest
@@ -1469,7 +1531,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
 }
 
 template <int G, int K, bool SMEM, int PIVOT, bool LIST>
-__global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const SearchParams prm)
+__global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
 {
     constexpr int WP = G * K;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1518,7 +1580,7 @@ __global__ void __launch_bounds__(K >= 4 ? 512 : 1024) search_kernel(const Searc
 // bulk-copied to shared memory, root frame queued, search, reduction into the
 // graph's own result array.
 template <int G, int K, bool SMEM, int PIVOT>
-__global__ void __launch_bounds__(K >= 4 ? 512 : 1024) batch_kernel(const BatchParams bp)
+__global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
 {
     constexpr int WP = G * K;
     extern __shared__ __align__(128) unsigned char smem_raw[];

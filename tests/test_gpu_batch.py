@@ -75,7 +75,7 @@ def test_batch_equals_alone_and_replays(ctx, mce):
         g.free()
 
 
-@pytest.mark.parametrize("kw", [dict(threads=32), dict(threads=1024), dict(blocks=1, threads=64),
+@pytest.mark.parametrize("kw", [dict(threads=32), dict(threads=512), dict(blocks=1, threads=64),
                                 dict(lanes=32, words=1), dict(stack_levels=3, queue_log2=18)])
 def test_batch_launch_shapes(ctx, mce, kw):
     sizes = (33, 70, 140) if "stack_levels" in kw else (33, 70, 140, 250, 400)

@@ -179,6 +179,9 @@ def test_invalid_inputs(ctx, mce):
     with pytest.raises(mce.MceError):
         ctx.load_bitset(40, pad)
     g = ctx.load_bitset(40, rows)           # the valid one still loads
+    for bad_threads in (48, 544, 1024):     # not a multiple of 32, or above the 512-thread bound
+        r = g.enumerate(mce.options(threads=bad_threads), raise_on_error=False)
+        assert r["rc"] == mce.MCE_EINVAL
     assert g.enumerate()["count"] == oracle.tomita(40, synth.gnp(40, 0.5, 60))["count"]
     g.free()
 
