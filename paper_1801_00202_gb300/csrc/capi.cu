@@ -126,14 +126,11 @@ void pick_shape(uint32_t n, const mce_options &o, int &G, int &K)
 
 // The search kernels are built for at most kMaxThreads threads per block
 // (128 registers per thread: the group state of four-word lanes, and no
-// spills for the narrower shapes).
+// spills for the narrower shapes), and the plain form launches that many.
+// On graphs of up to 128 vertices 512 threads beat 256 wherever the search
+// has real work (0.65-0.89x the time) and lost 3-9 % on the smallest,
+// launch-bound ones.
 constexpr unsigned kMaxThreads = 512u;
-
-unsigned default_threads(uint32_t n)
-{
-    const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
-    return W <= 4 ? 256u : kMaxThreads;
-}
 
 // stack_cap: most shared memory for the explicit stack per block (the served
 // form keeps blocks small so that several requests share an SM).
@@ -163,7 +160,7 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode, c.list);
     if (search_smem(n, c.wp, c.smem, c.list) > limit) return MCE_EINVAL;
 
-    c.threads = o.threads_per_block ? o.threads_per_block : default_threads(n);
+    c.threads = o.threads_per_block ? o.threads_per_block : kMaxThreads;
     if (c.threads % 32 || c.threads > kMaxThreads) return MCE_EINVAL;
     const size_t base = search_smem(n, c.wp, c.smem, c.list);
     const size_t cap = stack_cap < limit - base ? base + stack_cap : limit;
