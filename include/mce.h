@@ -276,7 +276,10 @@ typedef struct {
                                      CSR offsets: clique i is list_ids[
                                      list_off[i] .. list_off[i+1]), count + 1
                                      entries are written                    */
-    uint64_t list_off_cap;
+    uint64_t list_off_cap;        /* (pinned buffers take one device copy;
+                                     pageable ones of 32 MB and more go
+                                     through two 32 MB pinned halves that the
+                                     context allocates on first use)        */
     uint64_t list_ids_needed;     /* out: sum of the clique sizes           */
     double kernel_ms, total_ms;
 } mce_result;

@@ -366,8 +366,11 @@ class Graph:
                "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
                "kernel_ms": r.kernel_ms, "total_ms": r.total_ms, "list_ids_needed": r.list_ids_needed}
         if listing and rc == 0:
-            out["list_off"] = off[:r.count + 1].copy()
-            out["list_ids"] = ids[:r.list_ids_needed].copy()
+            # exact capacities (the usual case) hand back the buffers as they
+            # are; larger ones are trimmed by a copy
+            no, ni = r.count + 1, r.list_ids_needed
+            out["list_off"] = off if off.size == no else off[:no].copy()
+            out["list_ids"] = ids if ids.size == ni else ids[:ni].copy()
         return out
 
 

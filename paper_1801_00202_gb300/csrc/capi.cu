@@ -421,6 +421,9 @@ struct mce_ctx {
     Server *server = nullptr;  // started by the first mce_submit
     std::mutex tune_mu;        // autotuned batch choices by (words class, pivot)
     std::map<uint32_t, TuneChoice> tuned;
+    std::mutex stage_mu;       // two pinned halves for copies to pageable host memory
+    void *stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
 };
 
 struct mce_graph {
@@ -539,6 +542,10 @@ extern "C" void mce_ctx_destroy(mce_ctx *ctx)
         DevicePick pick(ctx->device);
         server_stop(ctx);
         cudaStreamSynchronize(ctx->stream);
+        for (int i = 0; i < 2; ++i) {
+            if (ctx->stage[i]) cudaFreeHost(ctx->stage[i]);
+            if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
+        }
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     }
@@ -808,6 +815,66 @@ int list_alloc(mce_ctx *ctx, uint32_t n, const Config &c, const mce_result *res,
     return cuda_code(cudaMemsetAsync(m, 0, o_path, s));  // control words and fill counts
 }
 
+constexpr size_t kStageBytes = 32u << 20;  // one pinned staging half
+
+// memcpy split over up to 8 host threads (a pageable destination is written
+// at the speed of the threads that touch it).
+void host_copy(unsigned char *dst, const unsigned char *src, size_t bytes)
+{
+    const unsigned t = (unsigned)std::min<size_t>(8, std::max<size_t>(1, bytes >> 22));
+    const size_t part = (bytes + t - 1) / t;
+    std::vector<std::thread> th;
+    for (unsigned i = 1; i < t; ++i) {
+        const size_t b = i * part, e = std::min(bytes, b + part);
+        if (b < e) th.emplace_back([=] { std::memcpy(dst + b, src + b, e - b); });
+    }
+    std::memcpy(dst, src, std::min(bytes, part));
+    for (auto &x : th) x.join();
+}
+
+// Device-to-host copy, complete on return.  A pinned or registered
+// destination takes one copy; a large pageable one goes through the
+// context's two pinned staging halves, the device copy of each chunk
+// overlapping the host copy of the one before.
+cudaError_t copy_to_host(mce_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    cudaPointerAttributes at{};
+    const bool pinned = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if (pinned || bytes < kStageBytes) {
+        const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+        return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (!ctx->stage[i]) e = cudaHostAlloc(&ctx->stage[i], kStageBytes, cudaHostAllocDefault);
+        if (e == cudaSuccess && !ctx->stage_ev[i])
+            e = cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming);
+    }
+    unsigned char *d = static_cast<unsigned char *>(dst);
+    const unsigned char *sp = static_cast<const unsigned char *>(src);
+    const size_t chunks = (bytes + kStageBytes - 1) / kStageBytes;
+    for (size_t i = 0; i <= chunks && e == cudaSuccess; ++i) {
+        if (i < chunks) {  // half i & 1 was emptied by the host copy of chunk i - 2
+            const size_t off = i * kStageBytes;
+            e = cudaMemcpyAsync(ctx->stage[i & 1], sp + off, std::min(kStageBytes, bytes - off),
+                                cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->stage_ev[i & 1], s);
+        }
+        if (e == cudaSuccess && i > 0) {
+            const size_t j = i - 1, off = j * kStageBytes;
+            e = cudaEventSynchronize(ctx->stage_ev[j & 1]);
+            if (e == cudaSuccess)
+                host_copy(d + off, static_cast<const unsigned char *>(ctx->stage[j & 1]),
+                          std::min(kStageBytes, bytes - off));
+        }
+    }
+    if (e != cudaSuccess) cudaStreamSynchronize(s);  // no copy into a staging half stays in flight
+    return e;
+}
+
 // CSR listing from a finished listing search (result words h) into the
 // caller's host buffers.
 int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d_order,
@@ -852,8 +919,8 @@ int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d
     j.temp = m + ib + ob;
     j.temp_bytes = tb;
     e = list_build(j, s);
-    if (e == cudaSuccess && ids) e = cudaMemcpyAsync(res->list_ids, j.ids_out, ids * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(res->list_off, j.off_out, (count + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = copy_to_host(ctx, res->list_ids, j.ids_out, ids * 4, s);
+    if (e == cudaSuccess) e = copy_to_host(ctx, res->list_off, j.off_out, (count + 1) * 8, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dfree(ctx, mem, ib + ob + tb, s);
     return e == cudaSuccess ? MCE_OK : MCE_ECUDA;
