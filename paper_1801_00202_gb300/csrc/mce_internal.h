@@ -142,7 +142,7 @@ cudaError_t outer_csr_from_rows(uint32_t n, uint32_t w, const uint32_t *rows, ui
                                 void *temp, size_t temp_bytes, size_t *need, cudaStream_t s);
 // Degeneracy order (minimum remaining degree first, smallest label on ties):
 // order[i] = vertex i, pos[v] = its position.  One block; n <= 65535 and
-// every degree < 65535.
+// every degree < 65535; off/adj a symmetric adjacency.
 cudaError_t outer_degeneracy(uint32_t n, const uint32_t *off, const uint32_t *adj, uint32_t *order, uint32_t *pos,
                              cudaStream_t s);
 // Fill every subproblem's rows, labels, root sets and table[i].rv (one block

@@ -132,48 +132,96 @@ __global__ void row_fill_kernel(uint32_t n, uint32_t w, const uint32_t *__restri
 
 // ---------------------------------------------------------------------------
 // Degeneracy order, one block: every round takes the remaining vertex of
-// smallest (degree, label) and lowers its remaining neighbours' degrees.
-// Degrees live in shared memory as 16-bit values; 0xffff marks removed.
+// smallest key (degree << 16 | label) and lowers its remaining neighbours'
+// degrees.  Degrees live in shared memory as 16-bit values (0xffff marks a
+// removed vertex); the smallest key of every chunk of 32 vertices and of
+// every super-chunk of 32 chunks is kept beside them.  A lowered degree only
+// lowers keys, so it updates both minima with atomicMin; the removed
+// vertex's chunk and super-chunk are recomputed.  Warp 0 picks the vertex
+// (from the at most 64 super-chunk minima) and recomputes the minima; the
+// whole block lowers the neighbours' degrees; two barriers per round.  With
+// SOFF the offsets are staged in shared memory too (one global round trip
+// fewer per round).
 
-__global__ void __launch_bounds__(1024) degeneracy_kernel(uint32_t n, const uint32_t *__restrict__ off,
-                                                          const uint32_t *__restrict__ adj, uint32_t *order,
-                                                          uint32_t *pos)
+constexpr unsigned kDegeneracyThreads = 256;
+
+__device__ __forceinline__ unsigned degeneracy_key(const uint16_t *sdeg, uint32_t n, uint32_t v)
 {
-    extern __shared__ uint16_t sdeg[];
-    __shared__ unsigned wmin[32];
+    if (v >= n) return FULLM;
+    const unsigned d = sdeg[v];
+    return d == 0xffffu ? FULLM : ((d << 16) | v);
+}
+
+template <bool SOFF>
+__global__ void __launch_bounds__(kDegeneracyThreads) degeneracy_kernel(uint32_t n, const uint32_t *__restrict__ goff,
+                                                                        const uint32_t *__restrict__ adj,
+                                                                        uint32_t *order, uint32_t *pos)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ unsigned chosen;
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) sdeg[v] = (uint16_t)(off[v + 1] - off[v]);
+    const uint32_t C = (n + 31u) / 32u, C2 = (C + 31u) / 32u;
+    unsigned *cmin = reinterpret_cast<unsigned *>(dsm);  // C chunk minima
+    unsigned *cmin2 = cmin + C;                          // C2 super-chunk minima
+    uint32_t *soff = cmin2 + C2;                         // n + 1 offsets (SOFF)
+    uint16_t *sdeg = reinterpret_cast<uint16_t *>(SOFF ? soff + n + 1 : soff);
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (SOFF)
+        for (uint32_t v = threadIdx.x; v <= n; v += blockDim.x) soff[v] = __ldg(goff + v);
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) sdeg[v] = (uint16_t)(__ldg(goff + v + 1) - __ldg(goff + v));
     __syncthreads();
+    const uint32_t *off = SOFF ? soff : goff;
+    for (uint32_t c = warp; c < C; c += nw) {
+        const unsigned k = __reduce_min_sync(FULLM, degeneracy_key(sdeg, n, c * 32u + lane));
+        if (lane == 0) cmin[c] = k;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (uint32_t c2 = 0; c2 < C2; ++c2) {
+            const uint32_t c = c2 * 32u + lane;
+            const unsigned k = __reduce_min_sync(FULLM, c < C ? cmin[c] : FULLM);
+            if (lane == 0) cmin2[c2] = k;
+        }
+    }
     for (uint32_t i = 0; i < n; ++i) {
-        unsigned best = FULLM;
-        for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-            const unsigned d = sdeg[v];
-            if (d != 0xffffu) {
-                const unsigned key = (d << 16) | v;
-                best = key < best ? key : best;
+        if (warp == 0) {
+            unsigned best = FULLM;
+            for (uint32_t j = lane; j < C2; j += 32u) best = min(best, cmin2[j]);
+            best = __reduce_min_sync(FULLM, best);
+            if (lane == 0) {
+                chosen = best;
+                if (best != FULLM) {
+                    order[i] = best & 0xffffu;
+                    pos[best & 0xffffu] = i;
+                }
             }
         }
-        best = __reduce_min_sync(FULLM, best);
-        if (lane == 0) wmin[warp] = best;
         __syncthreads();
-        if (warp == 0) {
-            unsigned b = lane < nwarps ? wmin[lane] : FULLM;
-            b = __reduce_min_sync(FULLM, b);
-            if (lane == 0) chosen = b;
+        const unsigned best = chosen;
+        if (best == FULLM) break;  // nothing left (only on an asymmetric adjacency)
+        const uint32_t v = best & 0xffffu;
+        const uint32_t e = off[v + 1];
+        for (uint32_t k = off[v] + threadIdx.x; k < e; k += blockDim.x) {
+            const uint32_t u = __ldg(adj + k);  // a list holds u once: no two threads write sdeg[u]
+            const unsigned d = sdeg[u];
+            if (d == 0xffffu) continue;
+            sdeg[u] = (uint16_t)(d - 1u);
+            // minima only fall until warp 0 recomputes them after the
+            // barrier, so a stored minimum at or below the key needs no atomic
+            const unsigned key = ((d - 1u) << 16) | u;
+            if (key < cmin[u >> 5]) atomicMin(cmin + (u >> 5), key);
+            if (key < cmin2[u >> 10]) atomicMin(cmin2 + (u >> 10), key);
         }
+        if (threadIdx.x == 0) sdeg[v] = 0xffffu;
         __syncthreads();
-        const uint32_t v = chosen & 0xffffu;
-        if (threadIdx.x == 0) {
-            order[i] = v;
-            pos[v] = i;
-            sdeg[v] = 0xffffu;
+        if (warp == 0) {  // v's chunk and super-chunk, read before the next pick
+            const unsigned kc = __reduce_min_sync(FULLM, degeneracy_key(sdeg, n, (v & ~31u) + lane));
+            if (lane == 0) cmin[v >> 5] = kc;
+            __syncwarp();
+            const uint32_t c = (v >> 10) * 32u + lane;
+            const unsigned k2 = __reduce_min_sync(FULLM, c < C ? cmin[c] : FULLM);
+            if (lane == 0) cmin2[v >> 10] = k2;
+            __syncwarp();
         }
-        for (uint32_t e = off[v] + threadIdx.x; e < off[v + 1]; e += blockDim.x) {
-            const uint32_t u = adj[e];
-            if (sdeg[u] != 0xffffu) sdeg[u] = (uint16_t)(sdeg[u] - 1u);
-        }
-        __syncthreads();
     }
 }
 
@@ -338,10 +386,22 @@ cudaError_t outer_degeneracy(uint32_t n, const uint32_t *off, const uint32_t *ad
                              cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    const size_t smem = ((size_t)n * 2 + 15) / 16 * 16;
-    cudaError_t e = kernel_smem_setup((const void *)degeneracy_kernel);
+    const size_t C = (n + 31u) / 32u, C2 = (C + 31u) / 32u;
+    const size_t plain = ((C + C2) * 4 + (size_t)n * 2 + 15) / 16 * 16;
+    const size_t staged = plain + ((size_t)n + 1) * 4;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    degeneracy_kernel<<<1, 1024, smem, s>>>(n, off, adj, order, pos);
+    if (staged + 1024 <= (size_t)optin) {
+        e = kernel_smem_setup((const void *)degeneracy_kernel<true>);
+        if (e != cudaSuccess) return e;
+        degeneracy_kernel<true><<<1, kDegeneracyThreads, staged, s>>>(n, off, adj, order, pos);
+    } else {
+        e = kernel_smem_setup((const void *)degeneracy_kernel<false>);
+        if (e != cudaSuccess) return e;
+        degeneracy_kernel<false><<<1, kDegeneracyThreads, plain, s>>>(n, off, adj, order, pos);
+    }
     return cudaGetLastError();
 }
 

@@ -78,6 +78,33 @@ def test_sparse_graphs_beyond_the_bitset_path(ctx, mce, n, p, seed):
     expect_outer(got, n, uv, what=f"G({n},{p})")
 
 
+def test_outer_with_offsets_beyond_shared_memory(ctx, mce):
+    """n = 60,000 as 15,000 disjoint K4: too many vertices for the
+    degeneracy kernel to stage the offsets in shared memory beside the
+    degrees, so it reads them from global memory.  The order finishes one K4
+    before the next (the others keep degree 3 while the current one's drop),
+    every component runs the same subproblems, so the counters are 15,000
+    times those of one K4 in the oracle, and the hash is the sum of the
+    15,000 clique hashes."""
+    k = 15000
+    one = oracle.outer(4, synth.complete(4))
+    pairs = np.array([(a, b) for a in range(4) for b in range(a + 1, 4)], dtype=np.uint32)
+    uv = ((np.arange(k, dtype=np.uint32) * 4)[:, None, None] + pairs[None, :, :]).reshape(-1, 2)
+    g = ctx.load_edges(4 * k, uv)
+    try:
+        got = g.enumerate()
+    finally:
+        g.free()
+    assert got["count"] == k * one["count"] == k
+    assert (got["nodes"], got["internal"], got["dead_ends"]) == \
+        (k * one["nodes"], k * one["internal"], k * one["dead_ends"])
+    h = 0
+    for c in range(k):
+        h = (h + oracle.clique_hash(np.arange(4 * c, 4 * c + 4))) & ((1 << 64) - 1)
+    assert got["hash"] == h
+    assert int(got["hist"][4]) == k and int(got["hist"].sum()) == k
+
+
 def test_sparse_limits(ctx, mce):
     # a vertex of degree >= MCE_NMAX has a subproblem beyond the bitset path
     n = 5000
