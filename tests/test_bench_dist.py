@@ -1,9 +1,10 @@
 """Host logic of bench.py's multi-rank runs, on CPU with the gloo backend
 (world size 2): every rank ends with the slowest rank's time, the job's rate
 counts every rank's units over that time, and the reference arm does its
-work on rank 0 only."""
+work on rank 0 only, printing one JSON line in the bench contract."""
 from __future__ import annotations
 
+import json
 import os
 import socket
 import subprocess
@@ -63,3 +64,23 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle on the host cores) needs no GPU and
+    prints one JSON line with the same metric, unit and workload as the GPU
+    arm, its own timing as value, cpu_baseline and e2e."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 0
+    assert d["unit"] == "maximal cliques/s" and d["higher_is_better"] is True
+    assert d["config"]["workload"].startswith("G(n=1000, p=0.3) seed 1")
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    cb, e2e = d["cpu_baseline"], d["e2e"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
