@@ -818,15 +818,22 @@ int list_alloc(mce_ctx *ctx, uint32_t n, const Config &c, const mce_result *res,
 constexpr size_t kStageBytes = 32u << 20;  // one pinned staging half
 
 // memcpy split over up to 8 host threads (a pageable destination is written
-// at the speed of the threads that touch it).
+// at the speed of the threads that touch it); a part whose thread cannot be
+// started is copied by the caller.
 void host_copy(unsigned char *dst, const unsigned char *src, size_t bytes)
 {
     const unsigned t = (unsigned)std::min<size_t>(8, std::max<size_t>(1, bytes >> 22));
     const size_t part = (bytes + t - 1) / t;
     std::vector<std::thread> th;
+    th.reserve(t);
     for (unsigned i = 1; i < t; ++i) {
         const size_t b = i * part, e = std::min(bytes, b + part);
-        if (b < e) th.emplace_back([=] { std::memcpy(dst + b, src + b, e - b); });
+        if (b >= e) continue;
+        try {
+            th.emplace_back([=] { std::memcpy(dst + b, src + b, e - b); });
+        } catch (...) {
+            std::memcpy(dst + b, src + b, e - b);
+        }
     }
     std::memcpy(dst, src, std::min(bytes, part));
     for (auto &x : th) x.join();
@@ -1781,7 +1788,12 @@ bool admit_batch(Server *sv)
         mce_batch_destroy(b);
         return false;
     }
-    MicroBatch *mb = new MicroBatch;
+    MicroBatch *mb = new (std::nothrow) MicroBatch;
+    if (!mb) {
+        cudaStreamSynchronize(s);
+        mce_batch_destroy(b);
+        return false;
+    }
     mb->b = b;
     mb->slot = slot;
     sv->busy[slot] = true;
