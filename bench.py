@@ -87,7 +87,7 @@ SERVE_LOAD, LATENCY_LOAD = 1.2, 0.7
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel built
 # from sources with this fingerprint; reported only while the sources match.
 KERNEL_SOURCES = ("search_impl.cuh", "search_inst.cuh", "mce_internal.h", "capi.cu")
-TRAFFIC = {"fingerprint": "a172d0761a24db49", "workload": "gnp_1000_0.3_s1", "bytes": 744_450 + 5_630,
+TRAFFIC = {"fingerprint": "97211f888ea92347", "workload": "gnp_1000_0.3_s1", "bytes": 744_450 + 5_630,
            "profile": "profiles/search_kernel_gnp1000_dram.md"}
 
 

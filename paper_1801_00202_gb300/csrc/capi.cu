@@ -1818,9 +1818,11 @@ void retire_batch(Server *sv, MicroBatch *mb, bool ok)
     mce_batch *b = mb->b;
     std::vector<uint64_t> h;
     float ms = 0.f;
-    if (ok) {
+    if (ok) {  // on the slot's own stream: no wait on other streams' work
         h.resize(b->out_words);
-        ok = cudaMemcpy(h.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+        cudaStream_t s = sv->streams[mb->slot];
+        ok = cudaMemcpyAsync(h.data(), b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+             cudaStreamSynchronize(s) == cudaSuccess;
         cudaEventElapsedTime(&ms, sv->ev0[mb->slot], sv->ev1[mb->slot]);
     }
     const auto now = std::chrono::steady_clock::now();
