@@ -13,6 +13,10 @@ What each function follows in the paper:
   renumbering (Section 4.2), BKPivotOrdered / ChoosePivotOrdered (Alg. 4)
   with the GreedyBB, GreedyBBTX or TomitaBB pivot (Section 4.3).
 * ``mdf_order`` -- the maximum-degree-first ordering alone (Section 4.2).
+* ``root_children`` / ``ordered_part`` -- the root's children of Alg. 4 as
+  independent subtrees (the decomposition Alg. 3 makes over vertices,
+  Section 3.3): the candidate-set size of every child, and the search of a
+  chosen set of children.
 * ``clique_hash`` / ``mix64`` -- the order-independent clique hash of the
   library's output contract (not in the paper; SplitMix64 finaliser).
 
@@ -62,6 +66,11 @@ def _load():
         lib.oracle_ordered.restype = C.c_int
         lib.oracle_ordered.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, u32p, u64p, u64p,
                                        u32p, C.c_uint64, u64p, i32p, C.c_uint64, u64p]
+        lib.oracle_root_children.restype = C.c_int
+        lib.oracle_root_children.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, u32p, C.c_uint32, u32p]
+        lib.oracle_ordered_part.restype = C.c_int
+        lib.oracle_ordered_part.argtypes = [C.c_uint32, u32p, u32p, C.c_int, u32p, C.POINTER(C.c_ubyte),
+                                            C.c_uint32, C.c_int, u64p, u64p]
         lib.oracle_degeneracy_order.restype = None
         lib.oracle_degeneracy_order.argtypes = [C.c_uint32, u32p, u32p, u32p]
         lib.oracle_outer.restype = C.c_int
@@ -172,6 +181,42 @@ def ordered(n: int, uv, mode: str = "greedy", order=None, listing: bool = False,
             i += 3 + k
         res["trace"] = recs
     return res
+
+
+def root_children(n: int, uv, mode: str = "greedy", order=None) -> np.ndarray:
+    """Candidate-set sizes |P_t| of the root's children t = 0, 1, ... of
+    Alg. 4 (the root's branching set in order)."""
+    lib = _load()
+    off, adj = csr(n, uv)
+    sizes = np.zeros(max(n, 1), dtype=np.uint32)
+    cnt = np.zeros(1, dtype=np.uint32)
+    ordv = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    rc = lib.oracle_root_children(n, _p(off, C.c_uint32), _p(adj if adj.size else np.zeros(1, np.uint32), C.c_uint32),
+                                  MODES[mode], _p(ordv, C.c_uint32), _p(sizes, C.c_uint32), sizes.size,
+                                  _p(cnt, C.c_uint32))
+    if rc:
+        raise MemoryError("oracle ran out of memory")
+    return sizes[:int(cnt[0])].copy()
+
+
+def ordered_part(n: int, uv, mode: str, children, count_root: bool, order=None):
+    """Alg. 4 searching only the root children listed in ``children``
+    (indices into the root's branching set); the root node is counted only
+    when ``count_root``."""
+    lib = _load()
+    off, adj = csr(n, uv)
+    sel = np.zeros(max(n, 1), dtype=np.uint8)
+    for t in children:
+        sel[int(t)] = 1
+    stats = np.zeros(5, dtype=np.uint64)
+    hist = np.zeros(n + 1, dtype=np.uint64)
+    ordv = None if order is None else np.ascontiguousarray(order, dtype=np.uint32)
+    rc = lib.oracle_ordered_part(n, _p(off, C.c_uint32), _p(adj if adj.size else np.zeros(1, np.uint32), C.c_uint32),
+                                 MODES[mode], _p(ordv, C.c_uint32), _p(sel, C.c_ubyte), sel.size,
+                                 1 if count_root else 0, _p(stats, C.c_uint64), _p(hist, C.c_uint64))
+    if rc:
+        raise MemoryError("oracle ran out of memory")
+    return _result(stats, hist, n)
 
 
 def mdf_order(n: int, uv) -> np.ndarray:

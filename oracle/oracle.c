@@ -154,6 +154,9 @@ typedef struct {
     int32_t *trace;                 /* optional: first internal nodes        */
     uint64_t trace_cap, trace_used;
     uint64_t max_nodes;             /* 0 = unlimited; else stop after this   */
+    const unsigned char *root_sel;  /* optional: root children to expand    */
+    uint32_t root_sel_n;            /* entries of root_sel                   */
+    int count_root;                 /* with root_sel: count the root node    */
     int oom, stopped;
 } run_t;
 
@@ -278,10 +281,14 @@ static void bk_tomita(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t 
 static void bk_ordered(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t nx, uint32_t rn)
 {
     if (r->oom) return;
-    r->nodes++;
-    if (np == 0 && nx == 0) { report(r, rn); return; }
-    if (np == 0) { r->dead_ends++; return; }
-    r->internal++;
+    /* a part of the root's branching (root_sel): the root node itself is
+     * counted by one part only */
+    const int part_root = rn == 0 && r->root_sel != NULL;
+    const int counted = !part_root || r->count_root;
+    if (counted) r->nodes++;
+    if (np == 0 && nx == 0) { if (counted) report(r, rn); return; }
+    if (np == 0) { if (counted) r->dead_ends++; return; }
+    if (counted) r->internal++;
 
     /* ChoosePivotOrdered.  Sets hold positions, so element 0 is the vertex
      * earliest in the order; scanning ascending with strict '>' gives the
@@ -349,7 +356,11 @@ static void bk_ordered(run_t *r, uint32_t *P, uint32_t np, uint32_t *X, uint32_t
         uint32_t ncp = set_and(P, np, nv, dv, cP);
         uint32_t ncx = set_and(X, nx, nv, dv, cX);
         r->R[rn] = v;
-        bk_ordered(r, cP, ncp, cX, ncx, rn + 1);
+        /* a root child outside the part is skipped, but its move from P to
+         * X below still happens: later siblings see exactly the sets of the
+         * sequential loop */
+        if (!part_root || (t < r->root_sel_n && r->root_sel[t]))
+            bk_ordered(r, cP, ncp, cX, ncx, rn + 1);
         np = set_erase(P, np, v);
         nx = set_insert(X, nx, v);
     }
@@ -440,6 +451,46 @@ done:
     return rc;
 }
 
+/* The graph renumbered by position (Section 4.2, "How we use the vertex
+ * ordering"): position i is vertex ord[i]; its neighbours become positions,
+ * sorted, so the order is kept inside every set. */
+typedef struct {
+    uint32_t *ord, *pos, *roff, *radj;
+} renum_t;
+
+static void renum_free(renum_t *g)
+{
+    free(g->ord); free(g->pos); free(g->roff); free(g->radj);
+}
+
+/* order: NULL -> maximum-degree-first; else order[i] = vertex at position i. */
+static int renum_init(renum_t *g, uint32_t n, const uint32_t *off, const uint32_t *adj, const uint32_t *order)
+{
+    size_t nn = (size_t)(n ? n : 1);
+    uint32_t m2 = n ? off[n] : 0;
+    g->ord = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    g->pos = (uint32_t *)malloc(nn * sizeof(uint32_t));
+    g->roff = (uint32_t *)malloc((nn + 1) * sizeof(uint32_t));
+    g->radj = (uint32_t *)malloc((size_t)(m2 ? m2 : 1) * sizeof(uint32_t));
+    if (!g->ord || !g->pos || !g->roff || !g->radj) return -2;
+    if (order) memcpy(g->ord, order, (size_t)n * sizeof(uint32_t));
+    else oracle_mdf_order(n, off, adj, g->ord);
+    for (uint32_t i = 0; i < n; ++i) g->pos[g->ord[i]] = i;
+    g->roff[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t v = g->ord[i], k = g->roff[i];
+        for (uint32_t e = off[v]; e < off[v + 1]; ++e) g->radj[k++] = g->pos[adj[e]];
+        g->roff[i + 1] = k;
+        /* insertion sort of the new row (plain and obviously correct) */
+        for (uint32_t a = g->roff[i] + 1; a < k; ++a) {
+            uint32_t x = g->radj[a], b = a;
+            while (b > g->roff[i] && g->radj[b - 1] > x) { g->radj[b] = g->radj[b - 1]; --b; }
+            g->radj[b] = x;
+        }
+    }
+    return 0;
+}
+
 /* order: NULL -> maximum-degree-first; else order[i] = vertex at position i.
  * order_out (optional) receives the order used. */
 int oracle_ordered(uint32_t n, const uint32_t *off, const uint32_t *adj,
@@ -449,38 +500,14 @@ int oracle_ordered(uint32_t n, const uint32_t *off, const uint32_t *adj,
                    int32_t *trace, uint64_t trace_cap, uint64_t *trace_used)
 {
     run_t r;
+    renum_t g = {0};
     int rc = run_init(&r, n, hist, list, list_cap);
-    size_t nn = (size_t)(n ? n : 1);
-    uint32_t *ord = (uint32_t *)malloc(nn * sizeof(uint32_t));
-    uint32_t *pos = (uint32_t *)malloc(nn * sizeof(uint32_t));
-    uint32_t *roff = (uint32_t *)malloc((nn + 1) * sizeof(uint32_t));
-    uint32_t m2 = n ? off[n] : 0;
-    uint32_t *radj = (uint32_t *)malloc((size_t)(m2 ? m2 : 1) * sizeof(uint32_t));
     uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
     uint32_t *X = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
-    if (rc || !ord || !pos || !roff || !radj || !P || !X) { rc = -2; goto done; }
+    if (rc || !P || !X || renum_init(&g, n, off, adj, order)) { rc = -2; goto done; }
+    if (order_out) memcpy(order_out, g.ord, (size_t)n * sizeof(uint32_t));
 
-    if (order) memcpy(ord, order, (size_t)n * sizeof(uint32_t));
-    else oracle_mdf_order(n, off, adj, ord);
-    if (order_out) memcpy(order_out, ord, (size_t)n * sizeof(uint32_t));
-    for (uint32_t i = 0; i < n; ++i) pos[ord[i]] = i;
-
-    /* Renumber: position i is vertex ord[i]; its neighbours become positions,
-     * sorted, so the order is kept inside every set (Section 4.2). */
-    roff[0] = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        uint32_t v = ord[i], k = roff[i];
-        for (uint32_t e = off[v]; e < off[v + 1]; ++e) radj[k++] = pos[adj[e]];
-        roff[i + 1] = k;
-        /* insertion sort of the new row (plain and obviously correct) */
-        for (uint32_t a = roff[i] + 1; a < k; ++a) {
-            uint32_t x = radj[a], b = a;
-            while (b > roff[i] && radj[b - 1] > x) { radj[b] = radj[b - 1]; --b; }
-            radj[b] = x;
-        }
-    }
-
-    r.off = roff; r.adj = radj; r.label = ord; r.mode = mode;
+    r.off = g.roff; r.adj = g.radj; r.label = g.ord; r.mode = mode;
     r.trace = trace; r.trace_cap = trace ? trace_cap : 0;
     for (uint32_t i = 0; i < n; ++i) P[i] = i;
     bk_ordered(&r, P, n, X, 0, 0);
@@ -488,7 +515,83 @@ int oracle_ordered(uint32_t n, const uint32_t *off, const uint32_t *adj,
     run_stats(&r, stats, list_used);
     if (trace_used) *trace_used = r.trace_used;
 done:
-    free(ord); free(pos); free(roff); free(radj); free(P); free(X);
+    renum_free(&g); free(P); free(X);
+    run_free(&r);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The root's children as independent subtrees.  Alg. 3 (Section 3.3) splits
+ * the enumeration into independent subproblems, one per vertex, because the
+ * sequential loop of Alg. 2 hands each branch the sets P n N(v), X n N(v)
+ * fixed by the branches before it.  The same holds for the root of Alg. 4:
+ * child t (the t-th vertex v_t of the root's branching set L, in order) is
+ * the search from R = {v_t}, P = (V minus v_1..v_{t-1}) n N(v_t),
+ * X = {v_1..v_{t-1}} n N(v_t), whatever happens inside the other children.
+ * So a set of children can be searched on its own and the counters of a
+ * partition of the children add up (modulo 2^64) to the whole search, the
+ * root node being counted by one part. */
+
+/* The root's branching set: its size to *count and, for t < cap,
+ * sizes[t] = |P_t| = |(V minus v_1..v_{t-1}) n N(v_t)|, the candidate set of
+ * child t (an estimate of its subtree's size). */
+int oracle_root_children(uint32_t n, const uint32_t *off, const uint32_t *adj, int mode, const uint32_t *order,
+                         uint32_t *sizes, uint32_t cap, uint32_t *count)
+{
+    renum_t g = {0};
+    uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    uint32_t *L = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    int rc = 0;
+    *count = 0;
+    if (!P || !L || renum_init(&g, n, off, adj, order)) { rc = -2; goto done; }
+    if (n == 0) goto done;
+    for (uint32_t i = 0; i < n; ++i) P[i] = i;
+    uint32_t np = n, p = 0;
+    if (mode == 2) {
+        /* TomitaBB with X empty: argmax over P of |P n N(u)| = the degree,
+         * earliest position on ties */
+        uint32_t best = 0;
+        for (uint32_t u = 0; u < n; ++u) {
+            uint32_t d = g.roff[u + 1] - g.roff[u];
+            if (u == 0 || d > best) { best = d; p = u; }
+        }
+    }
+    /* every other rule takes the first vertex of P when X is empty */
+    uint32_t nl = set_minus(P, np, g.radj + g.roff[p], g.roff[p + 1] - g.roff[p], L);
+    for (uint32_t t = 0; t < nl; ++t) {
+        uint32_t v = L[t];
+        uint32_t c = set_and_count(P, np, g.radj + g.roff[v], g.roff[v + 1] - g.roff[v]);
+        if (t < cap) sizes[t] = c;
+        np = set_erase(P, np, v);
+    }
+    *count = nl;
+done:
+    renum_free(&g); free(P); free(L);
+    return rc;
+}
+
+/* Alg. 4 restricted to the root children t with sel[t] != 0 (t < nsel);
+ * the root node is counted only when count_root. */
+int oracle_ordered_part(uint32_t n, const uint32_t *off, const uint32_t *adj, int mode, const uint32_t *order,
+                        const unsigned char *sel, uint32_t nsel, int count_root, uint64_t *stats, uint64_t *hist)
+{
+    run_t r;
+    renum_t g = {0};
+    int rc = run_init(&r, n, hist, NULL, 0);
+    uint32_t *P = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    uint32_t *X = (uint32_t *)malloc((size_t)(n + 1) * sizeof(uint32_t));
+    static const unsigned char none = 0;
+    if (rc || !P || !X || renum_init(&g, n, off, adj, order)) { rc = -2; goto done; }
+    r.off = g.roff; r.adj = g.radj; r.label = g.ord; r.mode = mode;
+    r.root_sel = sel ? sel : &none;
+    r.root_sel_n = sel ? nsel : 0;
+    r.count_root = count_root;
+    for (uint32_t i = 0; i < n; ++i) P[i] = i;
+    bk_ordered(&r, P, n, X, 0, 0);
+    rc = r.oom ? -2 : 0;
+    run_stats(&r, stats, NULL);
+done:
+    renum_free(&g); free(P); free(X);
     run_free(&r);
     return rc;
 }

@@ -312,6 +312,39 @@ def test_section5_example():
         assert tuple(labels[v] for v in L) == L_want
 
 
+def _tie_example():
+    order, edges, cliques, expect = None, [], [], {}
+    for line in open(os.path.join(GOLDEN, "tx_tie_example.txt")):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "order":
+            order = [int(x) for x in t[1:]]
+        elif t[0] == "edge":
+            edges.append((int(t[1]), int(t[2])))
+        elif t[0] == "clique":
+            cliques.append(tuple(int(x) for x in t[1:]))
+        else:
+            i = t.index(":")
+            expect[t[0]] = (int(t[1]), tuple(int(x) for x in t[i + 1:]))
+    return order, edges, cliques, expect
+
+
+def test_tx_tie_goes_to_the_earliest_vertex_of_x():
+    # Section 4.3: two vertices of X tie on |P n N(u)| at the node R = {5} of
+    # the hand-worked graph in tests/golden/tx_tie_example.txt; GreedyBBTX
+    # and GreedyBBNX must both pivot on the earlier one (3, not 4).
+    order, edges, cliques, expect = _tie_example()
+    n = len(order)
+    uv = np.array(edges, dtype=np.uint32)
+    assert brute_force(n, uv) == sorted(cliques)
+    for mode in ("tx", "nx", "greedy"):
+        r = oracle.ordered(n, uv, mode, order=np.array(order, dtype=np.uint32), listing=True, trace_cap=256)
+        assert r["listing"] == sorted(cliques)
+        node = [(p, L) for d, p, L in r["trace"] if d == 1 and 5 not in L and p in (2, 3, 4)]
+        assert node == [expect[mode]], (mode, r["trace"])
+
+
 # --- exact search-tree sizes of Alg. 4 --------------------------------------
 
 @pytest.mark.parametrize("n", [1, 2, 9, 100])
@@ -339,7 +372,7 @@ def test_tree_size_moon_moser(k):
 
 # --- statistical check against Table 1 --------------------------------------
 
-def _table1():
+def _table1_mu():
     rows = []
     with open(os.path.join(GOLDEN, "table1_random_mu.txt")) as f:
         for line in f:
@@ -349,7 +382,7 @@ def _table1():
     return rows
 
 
-@pytest.mark.parametrize("n,p,mu", _table1())
+@pytest.mark.parametrize("n,p,mu", _table1_mu())
 def test_table1_mean_mu(n, p, mu):
     """Mean mu over 10 seeded G(n, p) vs the paper's 10-graph mean and the
     textbook expectation (sanity only: different instances)."""
@@ -411,6 +444,54 @@ def test_steps_per_clique_match_table1(n, p):
         ours, theirs = steps / mu, paper[m] / paper["mu"]
         assert abs(ours / theirs - 1.0) < 0.06, (m, ours, theirs)
     assert got["tomita"][0] <= got["nx"][0] <= got["greedy"][0]
+
+
+# --- the root's children as independent subtrees (multi-GPU split) -----------
+
+@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita", "nx"])
+@pytest.mark.parametrize("n,p,seed", [(12, 0.5, 900), (16, 0.4, 901), (18, 0.6, 902)])
+def test_root_child_reports_the_cliques_it_owns(mode, n, p, seed):
+    # Child t of the root branches on v_t with v_1..v_{t-1} already moved to
+    # X, so it reports exactly the maximal cliques that contain v_t and none
+    # of v_1..v_{t-1} (brute force); the parts of any partition add up.
+    uv = synth.gnp(n, p, seed)
+    cliques = brute_force(n, uv)
+    whole = oracle.ordered(n, uv, mode, trace_cap=1 << 16)
+    depth, pivot, L = whole["trace"][0]
+    assert depth == 0
+    sizes = oracle.root_children(n, uv, mode)
+    assert len(sizes) == len(L)
+    tot = {"count": 0, "nodes": 0, "internal": 0, "dead_ends": 0, "hash": 0}
+    for t, v in enumerate(L):
+        own = [K for K in cliques if v in K and not set(L[:t]) & set(K)]
+        r = oracle.ordered_part(n, uv, mode, [t], count_root=(t == 0))
+        cnt, hist, h = summary(own, n)
+        assert (r["count"], r["hash"]) == (cnt, h) and np.array_equal(r["hist"], hist), (t, v)
+        for k in tot:
+            tot[k] = (tot[k] + r[k]) & MASK
+    for k in tot:
+        assert tot[k] == whole[k], k
+
+
+@pytest.mark.parametrize("mode", ["greedy", "tomita"])
+def test_root_children_sizes_and_partition_sums(mode):
+    # sizes on graphs worked by hand: the empty graph branches on every
+    # vertex with nothing left (sizes 0); K_n on one child with n - 1 others;
+    # Moon-Moser on k triangles branches on one triangle, each child keeping
+    # the other 3(k-1) vertices
+    assert oracle.root_children(7, synth.empty(7), mode).tolist() == [0] * 7
+    assert oracle.root_children(9, synth.complete(9), mode).tolist() == [8]
+    assert oracle.root_children(15, synth.moon_moser(5), mode).tolist() == [12, 12, 12]
+    # a two-way split of a larger graph adds up to the whole search
+    n, uv = 60, synth.gnp(60, 0.5, 903)
+    whole = oracle.ordered(n, uv, mode)
+    k = len(oracle.root_children(n, uv, mode))
+    a = oracle.ordered_part(n, uv, mode, range(0, k, 2), count_root=True)
+    b = oracle.ordered_part(n, uv, mode, range(1, k, 2), count_root=False)
+    for key in ("count", "nodes", "internal", "dead_ends"):
+        assert a[key] + b[key] == whole[key], key
+    assert (a["hash"] + b["hash"]) & MASK == whole["hash"]
+    assert np.array_equal(a["hist"] + b["hist"], whole["hist"])
 
 
 # --- Alg. 3: degeneracy-ordered outer loop ----------------------------------
