@@ -67,13 +67,34 @@ def select_workload(name: str):
 # Xeon E5-2690 v2 core (10-graph mean; other instances of the same shape).
 PAPER_CLIQUES_PER_S = 15487755 / 4.964
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
-# Roofline denominators derived from the GB300 unit counts and maximum clock:
-# 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz lane-operations per second (one
-# warp instruction per scheduler per clock), and 152 SMs x 128 B/clk x 2.07 GHz
-# of shared-memory bandwidth.
+# Roofline denominators: measured at the start of every run by
+# mce_measure_peaks (LOP3 lane-operations and 128-bit shared-memory load
+# bandwidth on every SM, CUDA events) -- see measure_peaks().  Until then,
+# and as context in the JSON line, the figures derived from the GB300 unit
+# counts and maximum clock: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+# lane-operations per second and 152 SMs x 128 B/clk x 2.07 GHz.
 SMS, SM_MHZ = 152, 2070.0
-ALU_PEAK_OPS = SMS * 4 * 32 * SM_MHZ * 1e6
-SMEM_PEAK_BPS = SMS * 128 * SM_MHZ * 1e6
+DERIVED_ALU_OPS = SMS * 4 * 32 * SM_MHZ * 1e6
+DERIVED_SMEM_BPS = SMS * 128 * SM_MHZ * 1e6
+ALU_PEAK_OPS = DERIVED_ALU_OPS
+SMEM_PEAK_BPS = DERIVED_SMEM_BPS
+PEAKS = {"source": "derived"}
+
+
+def measure_peaks(mce, device: int) -> dict:
+    """Measure the integer-pipe and shared-memory peaks on this GPU and make
+    them the roofline denominators of this run."""
+    global ALU_PEAK_OPS, SMEM_PEAK_BPS, PEAKS
+    pk = mce.mce_measure_peaks(device)
+    ALU_PEAK_OPS = pk["lop3_lane_ops_per_s"]
+    SMEM_PEAK_BPS = pk["lds_bytes_per_s"]
+    PEAKS = {"source": "measured: mce_measure_peaks (LOP3 / POPC lane-op and LDS.128 microbenchmarks, "
+                       "CUDA events, all SMs)",
+             "lop3_tops": pk["lop3_lane_ops_per_s"] / 1e12, "popc_tops": pk["popc_lane_ops_per_s"] / 1e12,
+             "lds_gbs": pk["lds_bytes_per_s"] / 1e9, "sm_count": pk["sm_count"],
+             "sm_clock_max_mhz": pk["sm_clock_max_khz"] / 1e3,
+             "derived_alu_tops": DERIVED_ALU_OPS / 1e12, "derived_lds_gbs": DERIVED_SMEM_BPS / 1e9}
+    return PEAKS
 ORACLE_SAMPLE_NODES = 1_500_000     # per reference step
 BASELINE_SAMPLE_NODES = 5_000_000   # cpu_baseline leg (about 10-30 s)
 # Batched form: 4096 G(n, p), n uniform in [32, 512], p uniform in [0.2, 0.8],
@@ -85,10 +106,10 @@ BATCH_GRAPHS = 4096
 SERVE_LOAD, LATENCY_LOAD = 1.2, 0.7
 # DRAM bytes (read + write) of one search-kernel launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel built
-# from sources with this fingerprint; reported only while the sources match.
-KERNEL_SOURCES = ("search_impl.cuh", "search_inst.cuh", "mce_internal.h", "capi.cu")
-TRAFFIC = {"fingerprint": "97211f888ea92347", "workload": "gnp_1000_0.3_s1", "bytes": 744_450 + 5_630,
-           "profile": "profiles/search_kernel_gnp1000_dram.md"}
+# from device sources with this fingerprint (sha256 of the files below, first
+# 16 hex digits); reported only while they match, else null.
+KERNEL_SOURCES = ("search_impl.cuh", "search_inst.cuh", "mce_internal.h")
+TRAFFIC = {"fingerprint": "", "workload": "gnp_1000_0.3_s1", "bytes": None}
 
 
 def words(n: int) -> int:
@@ -150,7 +171,7 @@ def kernel_fingerprint() -> str:
 
 
 def measured_traffic():
-    if TRAFFIC["workload"] == GOLDEN_KEY and TRAFFIC["fingerprint"] == kernel_fingerprint():
+    if TRAFFIC["bytes"] and TRAFFIC["workload"] == GOLDEN_KEY and TRAFFIC["fingerprint"] == kernel_fingerprint():
         return TRAFFIC["bytes"]
     return None
 
@@ -202,6 +223,54 @@ def cpu_baseline(uv, max_nodes: int) -> dict:
             "sample": f"Bron-Kerbosch with the Tomita pivot on the same graph, first {r['nodes']} search nodes "
                       f"({r['count']} maximal cliques, {dt:.1f} s on one host core)",
             "nodes_per_s": r["nodes"] / dt}
+
+
+def _oracle_part(job):
+    import oracle
+    n, uv, mode, children, count_root = job
+    t = time.perf_counter()
+    r = oracle.ordered_part(n, uv, mode, children, count_root)
+    return r["count"], r["nodes"], r["hash"], time.perf_counter() - t
+
+
+def cpu_split_baseline(n, uv, cores: int, mode: str = "greedy") -> dict:
+    """The oracle's Alg. 4 tree (the paper's GreedyBB) on all host cores: the
+    root's children partitioned by candidate-set size over `cores` spawned
+    processes (each an independent subtree), wall time of the whole search."""
+    import multiprocessing as mp
+
+    import oracle
+    from paper_1801_00202_gb300 import split
+    oracle.build()
+    sizes = oracle.root_children(n, uv, mode)
+    parts = [x for x in split.partition(sizes, cores)]
+    jobs = [(n, uv, mode, ch, i == 0) for i, ch in enumerate(parts) if ch or i == 0]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        pool.map(abs, range(len(jobs)))          # start the workers outside the timed region
+        t = time.perf_counter()
+        res = pool.map(_oracle_part, jobs, chunksize=1)
+        wall = time.perf_counter() - t
+    count = sum(c for c, _, _, _ in res)
+    nodes = sum(x for _, x, _, _ in res)
+    h = sum(x for _, _, x, _ in res) % (1 << 64)
+    return {"value": count / wall, "unit": UNIT, "cores": len(jobs), "kind": "oracle", "nodes_per_s": nodes / wall,
+            "seconds": wall, "count": count, "hash": h, "root_children": int(len(sizes)),
+            "busiest_part_s": max(x for _, _, _, x in res),
+            "sample": f"whole graph: the oracle's GreedyBB tree (Alg. 4), the root's {len(sizes)} children split "
+                      f"over {len(jobs)} host processes by candidate-set size"}
+
+
+def root_child_work(mce, ctx, n, uv) -> dict:
+    """Search nodes of every root child (mce_enumerate_part, one child per
+    call): the tree's imbalance as max / mean work per root child."""
+    g = ctx.load_edges(n, uv)
+    try:
+        sizes = g.root_children()
+        work = [g.enumerate_part([t], False)["nodes"] for t in range(len(sizes))]
+    finally:
+        g.free()
+    mean = sum(work) / max(1, len(work))
+    return {"children": len(work), "nodes_per_child": work, "max_over_mean": max(work) / mean if mean else None}
 
 
 # ---------------------------------------------------------------------------
@@ -511,6 +580,8 @@ def run_sweep(args):
             continue
         cell = {"n": row["n"], "p": row["p"], "paper_mu": row["mu"], "seeds": args.sweep_seeds}
         mus = []
+        seen = {}           # seed -> (count, hash) of the first pivot rule
+        consistent = True
         for pivot in ("greedy", "nx", "tomita"):
             nodes, internal, ms, total = [], [], [], []
             for seed in range(args.sweep_seeds):
@@ -518,6 +589,8 @@ def run_sweep(args):
                 torch.cuda.synchronize()
                 r = g.enumerate(mce.options(pivot=pivot))
                 g.free()
+                key = (r["count"], r["hash"], tuple(int(x) for x in r["hist"]))
+                consistent = consistent and seen.setdefault(seed, key) == key
                 if pivot == "greedy":
                     mus.append(r["count"])
                 nodes.append(r["nodes"])
@@ -533,6 +606,14 @@ def run_sweep(args):
             if not secs.startswith("<"):
                 cell[pivot]["speedup_vs_paper_core"] = float(secs) * 1e3 / statistics.mean(ms)
         cell["mu"] = statistics.mean(mus)
+        # the results do not depend on the pivot rule: the three rules must
+        # agree on every seed; where the oracle finishes in seconds
+        # (expected maximal cliques <= 3e5), seed 0 is checked against it
+        cell["pivot_rules_agree"] = consistent
+        if synth.expected_maximal_cliques(row["n"], row["p"]) <= 3e5:
+            import oracle
+            ref = oracle.tomita(row["n"], synth.gnp(row["n"], row["p"], 0))
+            cell["matches_oracle"] = seen[0] == (ref["count"], ref["hash"], tuple(int(x) for x in ref["hist"]))
         out.append(cell)
         print(json.dumps(cell), file=sys.stderr, flush=True)
     ctx.close()
@@ -570,9 +651,69 @@ def run_reference(args):
     return 0
 
 
+def run_sharded(args, mce, torch, dist, rank, world, local, dev):
+    """N > 1: one graph split over the ranks (the root's children are
+    independent subtrees; paper_1801_00202_gb300/split.py), strong scaling.
+    A step is this rank's share of the search (mce_enumerate_part: validate,
+    order, renumber, search its children; device time from the library's CUDA
+    events) and one all-reduce of the result vector."""
+    from paper_1801_00202_gb300 import split
+    uv = synth.gnp(N, P, SEED)
+    ctx = mce.Context(local)
+    g = ctx.load_edges(N, uv)
+    sizes = g.root_children()
+    mine = split.part_of(sizes, rank, world)
+    for _ in range(args.warmup):
+        split.all_reduce_result(g.enumerate_part(mine, rank == 0), N, dist, dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    dev_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.steps):
+        r = g.enumerate_part(mine, rank == 0)
+        dev_ms.append(r["kernel_ms"])
+        whole = split.all_reduce_result(r, N, dist, dev)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    g.free()
+    # end to end: the edge list from pinned host memory every step
+    pinned = torch.from_numpy(uv.astype(np.int32)).pin_memory()
+    host_uv = pinned.numpy().view(np.uint32)
+    dist.barrier()
+    wall = time.perf_counter()
+    for _ in range(args.steps):
+        g2 = ctx.load_edges(N, host_uv)
+        split.all_reduce_result(g2.enumerate_part(mine, rank == 0), N, dist, dev)
+        g2.free()
+    wall = time.perf_counter() - wall
+    total_ms, wall_ms = max_over_ranks([sum(dev_ms), 1e3 * wall], dist, dev)
+    ctx.close()
+    if rank != 0:
+        return 0
+    gold = golden()
+    line = base_line(args, world)
+    line["scaling"] = "strong"
+    line["config"].update({"parallelism": f"root children split over {world} GPUs", "replicas": 1})
+    line.update({"impl": "ours", "value": args.steps * whole["count"] / (total_ms / 1e3),
+                 "ms_per_step": total_ms / args.steps, "vs_baseline": None,
+                 "nodes_per_s": args.steps * whole["nodes"] / (total_ms / 1e3),
+                 "check": {"count": whole["count"], "hash": whole["hash"], "nodes": whole["nodes"],
+                           "matches_oracle": bool(gold) and whole["count"] == gold["count"]
+                           and whole["hash"] == gold["hash"] and whole["nodes"] == gold["greedy"]["nodes"]},
+                 "e2e": {"value": args.steps * whole["count"] / (wall_ms / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(uv.shape[0]) * 8, "d2h_bytes_per_step": 8 * (N + 22),
+                         "api": "per rank and step: mce_load_edges (pinned host edge list) + mce_enumerate_part + "
+                                "all-reduce of the result vector + mce_graph_free"},
+                 "gpu_launches": 7 * args.steps, "clocks": clk,
+                 "root_children": int(len(sizes))})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     forms_in = None
-    if not args.no_forms and int(os.environ.get("RANK", "0")) == 0:
+    if not args.no_forms and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         forms_in = generate_forms(args)     # host cores, before any CUDA call
     import torch
 
@@ -589,6 +730,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     mce.build()
     mce.lib()
+    if world > 1:
+        try:
+            return run_sharded(args, mce, torch, dist, rank, world, local, dev)
+        finally:
+            dist.destroy_process_group()
 
     uv = synth.gnp(N, P, SEED)
     W = words(N)
@@ -630,6 +776,7 @@ def run_ours(args):
     res = mce.decode_out(out, N)
     if res["status"] != 0:
         raise mce.MceError(res["status"], "warm-up")
+    peaks = measure_peaks(mce, local)
 
     clocks = ClockSampler(local)
     evs = [(mk(), mk(), mk()) for _ in range(args.steps)]
@@ -679,6 +826,11 @@ def run_ours(args):
         return 0
     configs = {name: plain_config(mce, torch, s, dev, name, n, cuv, 5, flush_l2)
                for name, n, cuv in other_configs()}
+    ictx = mce.Context(local, stream=s)
+    for name, n, cuv in other_configs():
+        if name.startswith("moon_moser"):
+            configs[name]["root_child_work"] = root_child_work(mce, ictx, n, cuv)
+    ictx.close()
     listing = listing_runs(mce, torch, local, s, uv)
 
     forms = None
@@ -718,14 +870,14 @@ def run_ours(args):
         "check": check,
         "roofline": {"bound": "alu", "kernel": "search_kernel",
                      "achieved": ops / (search_avg / 1e3) / 1e12, "peak": ALU_PEAK_OPS / 1e12,
-                     "unit": "Tops/s (32-bit lane ops)", "frac": ops / (search_avg / 1e3) / ALU_PEAK_OPS,
-                     "traffic": measured_traffic(), "traffic_source": TRAFFIC["profile"],
-                     "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz",
+                     "unit": "T lane-ops/s (32-bit LOP3)", "frac": ops / (search_avg / 1e3) / ALU_PEAK_OPS,
+                     "traffic": measured_traffic(), "traffic_fingerprint": kernel_fingerprint(),
+                     "peak_source": peaks["source"],
                      "ops_per_node": 6 * W, "nodes_per_launch": nodes},
         "roofline_smem": {"achieved": smem_bytes / (search_avg / 1e3) / 1e9, "peak": SMEM_PEAK_BPS / 1e9,
                           "unit": "GB/s", "frac": smem_bytes / (search_avg / 1e3) / SMEM_PEAK_BPS,
-                          "bytes_per_node": 8 * W,
-                          "peak_source": "derived: 152 SMs x 128 B/clk x 2.07 GHz"},
+                          "bytes_per_node": 8 * W, "peak_source": peaks["source"]},
+        "peaks": peaks,
         "e2e": None if args.no_e2e else {
             "value": job_rate(world, args.steps, r2["count"], 1e3 * e2e_total), "unit": UNIT,
             "h2d_bytes_per_step": int(uv.shape[0]) * 8,
@@ -740,6 +892,11 @@ def run_ours(args):
     })
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(uv, BASELINE_SAMPLE_NODES)
+        cores = max(1, min(os.cpu_count() or 1, 32))
+        allc = {DEFAULT_WORKLOAD: cpu_split_baseline(N, uv, cores)}
+        for name, n, cuv in other_configs():
+            allc[name] = cpu_split_baseline(n, cuv, cores)
+        line["cpu_baseline"]["all_cores"] = allc
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

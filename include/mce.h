@@ -238,19 +238,22 @@ int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_r
  * MCE_STATIC_SCRATCH_BYTES of device memory inside the library (one per GPU
  * that loads it, held until the process exits).  The paper has no
  * counterpart; this exists for callers that may not allocate device memory:
- * plug-ins whose host framework owns every allocation, request paths that
- * must not allocate per call, and code running inside a stream capture it
- * does not own.  The caller still owns d_rows and d_out.
- *  - The first call on each device looks up the area's address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ * plug-ins whose host framework owns every allocation, and request paths
+ * that must not allocate per call.  The caller still owns d_rows and d_out.
+ *  - Every call looks up the area's device address (cudaGetSymbolAddress,
+ *    with the calling thread's current device); the first call on a device
+ *    loads the library's device code there, so make it before any stream
+ *    capture.  A device reset invalidates nothing kept by the library: the
+ *    next call looks the area up again.
  *  - Every call reuses the same area; what must start from a known state is
  *    re-initialised by each call, but calls whose work overlaps on the GPU
  *    race on the area: do not issue overlapping calls (other streams, other
  *    host threads) on one device.
  *  - MCE_ENOMEM when the options need more scratch than the area holds
- *    (mce_scratch_bytes(n, opts) > MCE_STATIC_SCRATCH_BYTES); the default
- *    options fit for every n <= MCE_NMAX. */
+ *    (mce_scratch_bytes(n, opts) > MCE_STATIC_SCRATCH_BYTES).  The default
+ *    work queue grows with the number of resident subtree groups, so the
+ *    bound depends on the GPU: on a 152-SM GB300 the default options fit for
+ *    every n <= MCE_NMAX (at most about 27 MiB, for n <= 64). */
 #define MCE_STATIC_SCRATCH_BYTES (32u << 20)
 int mce_enumerate_device_static(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
                                 const mce_options *opts, uint64_t *d_out, void *stream);
@@ -311,6 +314,32 @@ void mce_graph_free(mce_graph *g);
  * MCE_ENOMEM if the device records of a listing that fits the caller's
  * buffers do not fit in device memory. */
 int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
+
+/* The root's children as independent subtrees (the split of one search
+ * over several GPUs).  Alg. 3 (Section 3.3) splits the enumeration into
+ * independent subproblems because each branch of the sequential loop gets
+ * sets fixed by the branches before it; the root of Alg. 4 splits the same
+ * way.  Its branching set L = V \ N(p0) (p0 the root's pivot under the
+ * chosen rule) is walked in order v_1, v_2, ...; child t (0-based) is the
+ * search from R = {v_t}, P = P_t n N(v_t), X = {v_1..v_{t-1}} n N(v_t),
+ * P_t = V minus v_1..v_{t-1}, and it reports exactly the maximal cliques
+ * that contain v_t and none of v_1..v_{t-1}.
+ *
+ * mce_root_children: |L| to *count and, for t < cap, sizes[t] = |P_t n
+ * N(v_t)| (host array, caller-owned): the size of child t's candidate set,
+ * an estimate of its subtree.  MCE_ETRUNC (with *count set) when cap < |L|.
+ *
+ * mce_enumerate_part: the search restricted to the children listed in
+ * children[0..k) (host array, strictly increasing indices < |L|, else
+ * MCE_EINVAL); the root node itself is counted only when count_root is
+ * non-zero.  Over a partition of 0..|L|-1 with exactly one part counting the
+ * root, count, nodes, internal, dead_ends, hash and hist add up (modulo
+ * 2^64) to mce_enumerate's.  Options as for mce_enumerate (no listing, no
+ * MCE_OUTER: MCE_ENOTIMPL); graphs held as adjacency lists (n > MCE_NMAX)
+ * have no single root: MCE_ENOTIMPL. */
+int mce_root_children(mce_graph *g, const mce_options *opts, uint32_t *sizes, uint32_t cap, uint32_t *count);
+int mce_enumerate_part(mce_graph *g, const mce_options *opts, const uint32_t *children, uint32_t k,
+                       int count_root, mce_result *res);
 
 /* Batched form.  mce_batch_create plans a batch of loaded graphs once:
  * graphs are grouped by subtree shape (lanes x words, chosen per graph like
@@ -387,6 +416,24 @@ const char *mce_strerror(int code);
  *   uint16 starving blocks (saturating).
  * Records past a block's share are dropped. */
 int mce_trace_enable(void *d_buf, uint64_t bytes);
+
+/* Throughput of the resources that bound the search (it does no dense
+ * contraction and, with the rows staged, no HBM traffic): LOP3 (the AND,
+ * ANDNOT, OR of set words) and POPC lane operations per second, and 128-bit
+ * shared-memory load bandwidth, each measured by a microbenchmark kernel
+ * with eight independent chains per thread on every SM of `device`, timed
+ * with CUDA events (about 0.1 s in all).  Also the SM count and the maximum
+ * SM clock from the device attributes.  Allocates a few bytes of device
+ * memory; changes no clock or other device setting. */
+typedef struct {
+    double lop3_lane_ops_per_s;
+    double popc_lane_ops_per_s;
+    double lds_bytes_per_s;
+    double ms_lop3, ms_popc, ms_lds;   /* per timed launch                  */
+    uint32_t sm_count;
+    uint32_t sm_clock_max_khz;
+} mce_peaks;
+int mce_measure_peaks(int device, mce_peaks *out);
 
 #ifdef __cplusplus
 }

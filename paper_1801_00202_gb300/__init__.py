@@ -62,6 +62,12 @@ class BatchBucket(C.Structure):
                 ("split_min_p", C.c_uint32), ("tuned", C.c_uint32), ("tuned_ms_per_graph", C.c_double)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("lop3_lane_ops_per_s", C.c_double), ("popc_lane_ops_per_s", C.c_double),
+                ("lds_bytes_per_s", C.c_double), ("ms_lop3", C.c_double), ("ms_popc", C.c_double),
+                ("ms_lds", C.c_double), ("sm_count", C.c_uint32), ("sm_clock_max_khz", C.c_uint32)]
+
+
 class Result(C.Structure):
     _fields_ = [("count", C.c_uint64), ("nodes", C.c_uint64), ("internal_nodes", C.c_uint64),
                 ("dead_ends", C.c_uint64), ("hash", C.c_uint64), ("max_size", C.c_uint32),
@@ -117,6 +123,9 @@ _SIGS = {
     "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
     "mce_strerror": (C.c_char_p, [C.c_int]),
     "mce_trace_enable": (C.c_int, [_VP, _U64]),
+    "mce_measure_peaks": (C.c_int, [C.c_int, C.POINTER(Peaks)]),
+    "mce_root_children": (C.c_int, [_VP, C.POINTER(Options), _VP, _U32, C.POINTER(_U32)]),
+    "mce_enumerate_part": (C.c_int, [_VP, C.POINTER(Options), _VP, _U32, C.c_int, C.POINTER(Result)]),
 }
 
 
@@ -168,6 +177,14 @@ def _check(rc: int, what: str) -> int:
 
 def mce_strerror(code: int) -> str:
     return lib().mce_strerror(code).decode()
+
+
+def mce_measure_peaks(device: int = 0) -> dict:
+    """LOP3 / POPC lane-ops per second and 128-bit shared-memory load bytes
+    per second measured on ``device`` (the search's roofline denominators)."""
+    pk = Peaks()
+    _check(lib().mce_measure_peaks(device, C.byref(pk)), "mce_measure_peaks")
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_}
 
 
 def mce_edges_to_rows(n, m, d_uv, words_per_row, d_rows, d_out, stream=None) -> int:
@@ -372,6 +389,37 @@ class Graph:
             out["list_off"] = off if off.size == no else off[:no].copy()
             out["list_ids"] = ids if ids.size == ni else ids[:ni].copy()
         return out
+
+
+    def root_children(self, opts: Options | None = None) -> np.ndarray:
+        """mce_root_children: candidate-set sizes of the root's children
+        (independent subtrees, in order)."""
+        cnt = C.c_uint32(0)
+        rc = lib().mce_root_children(self.handle, _opt(opts), None, 0, C.byref(cnt))
+        if rc not in (MCE_OK, MCE_ETRUNC):
+            _check(rc, "mce_root_children")
+        sizes = np.zeros(max(cnt.value, 1), dtype=np.uint32)
+        _check(lib().mce_root_children(self.handle, _opt(opts), sizes.ctypes.data, sizes.size, C.byref(cnt)),
+               "mce_root_children")
+        return sizes[:cnt.value].copy()
+
+    def enumerate_part(self, children, count_root: bool, opts: Options | None = None,
+                       raise_on_error: bool = True) -> dict:
+        """mce_enumerate_part: the search restricted to the listed root
+        children (strictly increasing indices); the root node is counted
+        only with count_root."""
+        ch = np.ascontiguousarray(np.asarray(children, dtype=np.uint32).reshape(-1))
+        hist = np.zeros(self.n + 1, dtype=np.uint64)
+        r = Result()
+        r.hist = hist.ctypes.data_as(C.POINTER(C.c_uint64))
+        r.hist_cap = hist.size
+        rc = lib().mce_enumerate_part(self.handle, _opt(opts), ch.ctypes.data if ch.size else None, ch.size,
+                                      1 if count_root else 0, C.byref(r))
+        if raise_on_error:
+            _check(rc, "mce_enumerate_part")
+        return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
+                "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
+                "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}
 
 
 def cliques(res: dict) -> list:

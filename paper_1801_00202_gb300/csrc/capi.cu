@@ -275,14 +275,30 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
         p.trace_per_block = (uint32_t)std::min<uint64_t>(g_trace_bytes / 16 / c.blocks, 0xffffffffu);
     }
     p.lst = lp ? *lp : ListParams{};
+    p.part = nullptr;
+    p.part_k = 0;
+    p.count_root = 1;
     return p;
 }
 
+// A part of the root's branching: d_children (device) lists k root-child
+// indices, strictly increasing.
+struct PartSpec {
+    const uint32_t *d_children;
+    uint32_t k;
+    uint32_t count_root;
+};
+
 int run_search(uint32_t n, const Config &c, const Layout &L, unsigned char *scratch, const uint32_t *rows,
                const uint32_t *order, uint64_t *out, const mce_options &o, cudaStream_t s,
-               const ListParams *lp = nullptr)
+               const ListParams *lp = nullptr, const PartSpec *part = nullptr)
 {
     SearchParams p = params(n, c, L, scratch, rows, order, out, o, lp);
+    if (part) {
+        p.part = part->d_children;
+        p.part_k = part->k;
+        p.count_root = part->count_root;
+    }
     LaunchShape sh{c.blocks, c.threads, c.smem_bytes, c.smem};
     return cuda_code(c.impl.run(p, sh, s));
 }
@@ -365,7 +381,7 @@ namespace {
 // configuration; lp non-null lists the cliques (host API).
 int enumerate_device_impl(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows, const mce_options &o,
                           const Config &c, const Layout &L, unsigned char *scr, uint64_t *d_out, cudaStream_t s,
-                          const ListParams *lp)
+                          const ListParams *lp, const PartSpec *part = nullptr)
 {
     uint32_t *order = reinterpret_cast<uint32_t *>(scr + L.order);
     uint32_t *rows = reinterpret_cast<uint32_t *>(scr + L.rows);
@@ -375,7 +391,7 @@ int enumerate_device_impl(uint32_t n, uint32_t words_per_row, const uint32_t *d_
         e = (o.flags & MCE_ORDER_IDENTITY) ? launch_identity(n, order, s) : launch_order(n, words_per_row, d_rows, order, s);
     if (e == cudaSuccess) e = launch_renumber(n, words_per_row, d_rows, order, c.wp, rows, s);
     if (e != cudaSuccess) return cuda_code(e);
-    return run_search(n, c, L, scr, rows, order, d_out, o, s, lp);
+    return run_search(n, c, L, scr, rows, order, d_out, o, s, lp, part);
 }
 
 }  // namespace
@@ -730,7 +746,10 @@ int fill_result(const std::vector<uint64_t> &h, uint32_t n, mce_result *res)
 }  // namespace
 
 namespace {
-int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0);
+// children / k / count_root: a part of the root's branching (children null:
+// the whole search).
+int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0,
+                   const uint32_t *children = nullptr, uint32_t k = 0, uint32_t count_root = 1);
 }
 
 namespace {
@@ -758,6 +777,89 @@ extern "C" int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *
         if (lg + 4 > 24) break;
         o.queue_log2 = lg + 4;
         rc = enumerate_once(g, o, res, t0);
+    }
+    return rc;
+}
+
+extern "C" int mce_root_children(mce_graph *g, const mce_options *opts, uint32_t *sizes, uint32_t cap,
+                                 uint32_t *count)
+{
+    if (!g || !count || (cap && !sizes)) return MCE_EINVAL;
+    if (!g->d_rows) return MCE_ENOTIMPL;  // sparse graphs: the outer loop has no single root
+    DevicePick pick(g->ctx->device);
+    mce_ctx *ctx = g->ctx;
+    const mce_options o = defaults(opts);
+    if (o.flags & (kListFlags | MCE_OUTER)) return MCE_ENOTIMPL;
+    Config c;
+    int rc = choose(g->n, o, c);
+    if (rc) return rc;
+    const Layout L = layout(g->n, c);
+    const uint32_t n = g->n;
+    // order | renumbered rows (scratch layout) | status words | pivot, count | sizes
+    const size_t o_stat = L.rows + round_up((size_t)n * c.wp * 4 + 16, 256);
+    const size_t o_piv = o_stat + 256, o_sizes = o_piv + 256;
+    const size_t bytes = o_sizes + round_up((size_t)std::max<uint32_t>(n, 1) * 4, 256);
+    void *mem = nullptr;
+    rc = dalloc(ctx, &mem, bytes);
+    if (rc != MCE_OK) return rc;
+    unsigned char *m = static_cast<unsigned char *>(mem);
+    uint32_t *order = reinterpret_cast<uint32_t *>(m + L.order);
+    uint32_t *rows = reinterpret_cast<uint32_t *>(m + L.rows);
+    uint64_t *stat = reinterpret_cast<uint64_t *>(m + o_stat);
+    unsigned *piv = reinterpret_cast<unsigned *>(m + o_piv);
+    uint32_t *d_count = piv + 1;
+    uint32_t *d_sizes = reinterpret_cast<uint32_t *>(m + o_sizes);
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(stat, 0, 64, s);
+    if (e == cudaSuccess) e = launch_validate_rows(n, g->w, g->d_rows, stat, s);  // status at stat[MCE_OUT_STATUS]
+    if (e == cudaSuccess)
+        e = (o.flags & MCE_ORDER_IDENTITY) ? launch_identity(n, order, s) : launch_order(n, g->w, g->d_rows, order, s);
+    if (e == cudaSuccess) e = launch_renumber(n, g->w, g->d_rows, order, c.wp, rows, s);
+    const bool tomita = o.pivot_mode == MCE_PIVOT_TOMITA;
+    if (e == cudaSuccess && tomita) e = launch_root_degree_pivot(rows, n, c.wp, piv, s);
+    if (e == cudaSuccess) e = launch_root_children(rows, n, c.wp, tomita ? piv : nullptr, d_sizes, n, d_count, s);
+    uint64_t st[MCE_OUT_STATUS + 1] = {0};
+    uint32_t cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st, stat, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_count, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && st[MCE_OUT_STATUS] == 0 && cnt && cap) {
+        e = cudaMemcpyAsync(sizes, d_sizes, (size_t)std::min(cap, cnt) * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    dfree(ctx, mem, bytes, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        return MCE_ECUDA;
+    }
+    if (st[MCE_OUT_STATUS]) return (int)(int64_t)st[MCE_OUT_STATUS];
+    *count = cnt;
+    return cnt > cap ? MCE_ETRUNC : MCE_OK;
+}
+
+extern "C" int mce_enumerate_part(mce_graph *g, const mce_options *opts, const uint32_t *children, uint32_t k,
+                                  int count_root, mce_result *res)
+{
+    if (!g || !res || (k && !children)) return MCE_EINVAL;
+    if (!g->d_rows) return MCE_ENOTIMPL;
+    for (uint32_t j = 1; j < k; ++j)
+        if (children[j] <= children[j - 1]) return MCE_EINVAL;
+    if (k && children[k - 1] >= g->n) return MCE_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    DevicePick pick(g->ctx->device);
+    mce_options o = defaults(opts);
+    if (o.flags & (kListFlags | MCE_OUTER)) return MCE_ENOTIMPL;
+    static const uint32_t none = 0;
+    const uint32_t *ch = k ? children : &none;  // non-null marks a part
+    int rc = enumerate_once(g, o, res, t0, ch, k, count_root ? 1u : 0u);
+    for (int tries = 0; rc == MCE_EOVERFLOW && tries < 2; ++tries) {
+        Config c;
+        if (choose(g->n, o, c) != MCE_OK) break;
+        uint32_t lg = 0;
+        while ((1u << lg) < std::max<uint32_t>(c.qcap, 2u * k)) ++lg;
+        if (lg + 4 > 24) break;
+        o.queue_log2 = lg + 4;
+        rc = enumerate_once(g, o, res, t0, ch, k, count_root ? 1u : 0u);
     }
     return rc;
 }
@@ -933,20 +1035,29 @@ int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d
     return e == cudaSuccess ? MCE_OK : MCE_ECUDA;
 }
 
-int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0)
+int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0,
+                   const uint32_t *children, uint32_t k, uint32_t count_root)
 {
     mce_ctx *ctx = g->ctx;
     const bool listing = (o.flags & kListFlags) != 0u;
     Config c;
     int rc = choose(g->n, o, c);
     if (rc) return rc;
+    if (children && c.qcap < 2u * k) c.qcap = next_pow2(2ull * k);  // every child frame queued at once
     const Layout L = layout(g->n, c);
-    const uint64_t sbytes = L.total;
+    const uint64_t sbytes = L.total + (children ? round_up((size_t)k * 4 + 4, 256) : 0);
     const size_t obytes = MCE_OUT_WORDS(g->n) * 8;
     void *scr = nullptr;
     uint64_t *d_out = nullptr;
     ListArea la;
+    PartSpec part{nullptr, k, count_root};
     rc = dalloc(ctx, &scr, sbytes);
+    if (rc == MCE_OK && children) {
+        uint32_t *dc = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(scr) + L.total);
+        part.d_children = dc;
+        if (k && cudaMemcpyAsync(dc, children, (size_t)k * 4, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+            rc = MCE_ECUDA;
+    }
     if (rc == MCE_OK) rc = dalloc(ctx, (void **)&d_out, obytes);
     if (rc == MCE_OK && listing) rc = list_alloc(ctx, g->n, c, res, la, ctx->stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -956,7 +1067,7 @@ int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chr
         cudaEventCreate(&e1);
         cudaEventRecord(e0, ctx->stream);
         rc = enumerate_device_impl(g->n, g->w, g->d_rows, o, c, L, static_cast<unsigned char *>(scr), d_out, ctx->stream,
-                                   listing ? &la.prm : nullptr);
+                                   listing ? &la.prm : nullptr, children ? &part : nullptr);
         cudaEventRecord(e1, ctx->stream);
         if (rc == MCE_OK) {
             cudaError_t e = cudaMemcpyAsync(h.data(), d_out, obytes, cudaMemcpyDeviceToHost, ctx->stream);

@@ -111,6 +111,13 @@ struct SearchParams {
     uint32_t trace_per_block;    // records per block
     Tuning tune;
     ListParams lst;              // clique listing (lst.rec null: off)
+    // A part of the root's branching (the root's children are independent
+    // subtrees): part (device, part_k entries, strictly increasing) lists
+    // the children searched; null searches the whole tree.  The root node is
+    // counted only with count_root.
+    const uint32_t *part;
+    uint32_t part_k;
+    uint32_t count_root;
 };
 
 // One graph of a batch (device table entry; pointers into library memory).
@@ -230,6 +237,20 @@ SearchImpl search_list_impl_32_1(bool smem, int pivot);
 SearchImpl search_list_impl_32_2(bool smem, int pivot);
 SearchImpl search_list_impl_32_4(bool smem, int pivot);
 
+
+// The root's children as independent subtrees (split.cu).  The root's
+// branching set is L = V \ N(p0) (p0 = root_pivot, or position 0 when null)
+// over the renumbered rows; child t branches on its t-th vertex v_t with
+// v_1..v_{t-1} moved from P to X.
+// sizes[t] = |P_t n N(v_t)|, P_t = V minus v_1..v_{t-1}, for t < cap;
+// *count = |L| (device words).
+cudaError_t launch_root_children(const uint32_t *rows, uint32_t n, uint32_t wp, const unsigned *root_pivot,
+                                 uint32_t *sizes, uint32_t cap, uint32_t *count, cudaStream_t s);
+// Queue frame j (< prm.part_k) = child prm.part[j] (after search_init_kernel
+// reserved the slots); an index beyond |L| or out of order sets MCE_EINVAL.
+cudaError_t launch_part_frames(const SearchParams &prm, const unsigned *root_pivot, cudaStream_t s);
+// TomitaBB's root pivot (the earliest vertex of maximum degree) to *dst.
+cudaError_t launch_root_degree_pivot(const uint32_t *rows, uint32_t n, uint32_t wp, unsigned *dst, cudaStream_t s);
 
 // Preprocessing kernels (prep.cu).
 cudaError_t launch_edges_to_rows(uint32_t n, uint64_t m, const uint32_t *uv, uint32_t w,

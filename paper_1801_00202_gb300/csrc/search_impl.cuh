@@ -1767,16 +1767,34 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
     const uint32_t n = prm.n;
     const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned nth = gridDim.x * blockDim.x;
-    for (unsigned i = tid; i < prm.qcap; i += nth) prm.seq[i] = (i == 0u && n > 0u) ? 1u : i;
+    // a part of the root's branching queues part_k child frames (written by
+    // the part-frames kernel that follows) and counts the root only when
+    // asked to
+    const bool part = prm.part != nullptr;
+    const unsigned queued = part ? prm.part_k : (n > 0u ? 1u : 0u);
+    const bool root = !part || prm.count_root;
+    for (unsigned i = tid; i < prm.qcap; i += nth) prm.seq[i] = i < queued ? i + 1u : i;
     for (unsigned i = tid; i < MCE_OUT_WORDS(n); i += nth) {
         if (i == MCE_OUT_STATUS) continue;  // sticky: an earlier step's error stays
         uint64_t v = 0ull;
-        if (i == MCE_OUT_NODES) v = 1ull;
-        if (n > 0u && i == MCE_OUT_INTERNAL) v = 1ull;
-        if (n == 0u && (i == MCE_OUT_COUNT || i == MCE_OUT_HIST)) v = 1ull;
-        if (n == 0u && i == MCE_OUT_HASH) v = mix64(0ull ^ mix64(0ull));
+        if (root && i == MCE_OUT_NODES) v = 1ull;
+        if (root && n > 0u && i == MCE_OUT_INTERNAL) v = 1ull;
+        if (root && n == 0u && (i == MCE_OUT_COUNT || i == MCE_OUT_HIST)) v = 1ull;
+        if (root && n == 0u && i == MCE_OUT_HASH) v = mix64(0ull ^ mix64(0ull));
         if (i == MCE_OUT_GROUPS) v = prm.total_groups;
         prm.out[i] = v;
+    }
+    if (part) {
+        if (tid == 0) {
+            Ctl *c = prm.ctl;
+            c->head = 0u;
+            c->abort = 0u;
+            const bool go = queued > 0u && prm.out[MCE_OUT_STATUS] == 0ull;
+            c->tail = go ? queued : 0u;
+            c->pending = go ? queued : 0u;
+            c->starving = 0u;
+        }
+        return;
     }
     if (n > 0u) {
         for (unsigned w = tid; w < (unsigned)WP; w += nth) {

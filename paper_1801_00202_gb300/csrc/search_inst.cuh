@@ -19,6 +19,10 @@ cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStr
     search_init_kernel<G, K><<<64, 256, 0, s>>>(prm, rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (prm.part) {
+        e = launch_part_frames(prm, rp, s);
+        if (e != cudaSuccess) return e;
+    }
     e = kernel_smem_setup((const void *)search_kernel<G, K, SMEM, PIVOT, LIST>);
     if (e != cudaSuccess) return e;
     search_kernel<G, K, SMEM, PIVOT, LIST><<<sh.blocks, sh.threads, sh.smem, s>>>(prm);

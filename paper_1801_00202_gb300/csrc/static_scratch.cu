@@ -5,23 +5,22 @@
 // Who needs this: callers that are handed input and output buffers but may
 // not allocate device memory themselves -- a plug-in or custom operator whose
 // host framework owns every device allocation (a serving runtime or a tensor
-// framework's caching allocator), latency-critical request paths that must
-// not pay for, or fragment memory with, an allocation per call, and code that
-// runs while someone else's stream capture is open, where an allocation call
-// would invalidate that capture.
+// framework's caching allocator), and latency-critical request paths that
+// must not pay for, or fragment memory with, an allocation per call.
 //
 // The area is MCE_STATIC_SCRATCH_BYTES of __device__ memory per GPU that
-// loads the library, held until the process exits.  Its device address is
-// looked up once per device (cudaGetSymbolAddress, with that device current)
-// on the first call made on that device; that first call should therefore
-// come before any stream capture.  Every call uses the same area and the
-// search re-initialises all of it that must start from zero or a known state
-// (queue tickets, control counters, root frame; the caller's d_out is zeroed
-// by the search too), but two calls whose work overlaps on the GPU -- on
-// different streams, or on one device from two host threads -- race on the
-// area and must not be issued.
+// loads the library, held until the process exits.  In host code the symbol
+// is only a stand-in, so its device address is looked up with
+// cudaGetSymbolAddress, with the device current, on every call: a device
+// reset, or a primary context released and created again, reloads the module
+// and may move the area, so no address is kept between calls.  The first
+// call on a device loads the module there; make it before any stream
+// capture.  Every call uses the same area and the search re-initialises all
+// of it that must start from zero or a known state (queue tickets, control
+// counters, root frame; the caller's d_out is zeroed by the search too), but
+// two calls whose work overlaps on the GPU -- on different streams, or on one
+// device from two host threads -- race on the area and must not be issued.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -31,28 +30,15 @@ static __device__ __align__(256) unsigned char g_static_scratch[MCE_STATIC_SCRAT
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-void *g_area[kMaxDevices] = {};
-
-// Device address of this device's area (looked up on first use).
+// Device address of the area on the current device, looked up afresh.
 int static_area(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return MCE_ECUDA;
     }
-    std::lock_guard<std::mutex> lk(g_lock);
-    if (!g_area[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return MCE_ECUDA;
-        }
-        g_area[dev] = p;
-    }
-    *out = g_area[dev];
+    *out = p;
     return MCE_OK;
 }
 

@@ -3,11 +3,16 @@ result it gives alone and the oracle's (count, histogram, hash, search-tree
 counters), whatever shapes the batch mixes."""
 from __future__ import annotations
 
+import os
+import sys
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
 
 pytestmark = pytest.mark.gpu
 
@@ -135,3 +140,34 @@ def test_autotuned_batch_matches_oracle_and_reuses_choices(ctx, mce):
     b2.close()
     for g in graphs:
         g.free()
+
+
+def _gen_batch_rows(i):
+    g = synth.batch_graph(i)
+    return g.n, synth.to_bitset(g.n, g.uv)
+
+
+def test_whole_batched_workload_matches_oracle(ctx, mce):
+    """All 4096 graphs of the batched workload (capped G(n, p), n in
+    [32, 512]) in one captured launch, each against the oracle's stored
+    count, hash, histogram and GreedyBB tree
+    (tests/golden/batch4096_results.txt)."""
+    import multiprocessing as mp
+    import make_workload_golden as mk
+    gold = mk.load("batch")
+    assert len(gold) == 4096
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        specs = pool.map(_gen_batch_rows, range(4096), chunksize=32)
+    graphs = [ctx.load_bitset(n, rows) for n, rows in specs]
+    b = mce.Batch(ctx, graphs)
+    res = b.run()
+    bad = []
+    for g, r in zip(gold, res):
+        hist = {k: int(v) for k, v in enumerate(r["hist"]) if v}
+        if (r["status"], r["count"], r["hash"], r["nodes"], r["internal"], r["dead_ends"], hist) != \
+                (0, g["count"], g["hash"], g["nodes"], g["internal"], g["dead_ends"], g["hist"]):
+            bad.append(g["index"])
+    b.close()
+    for g in graphs:
+        g.free()
+    assert not bad, bad[:20]

@@ -78,6 +78,15 @@ def test_pivot_rules(ctx, mce, mode, n, p, seed):
     expect_equal(run_host(ctx, mce, n, uv, pivot=mode), n, uv, mode=mode, what=f"{mode} G({n},{p})")
 
 
+@pytest.mark.parametrize("mode", ["tx", "tomita", "nx"])
+@pytest.mark.parametrize("n,p,seed", [(1100, 0.1, 33), (1500, 0.05, 34), (2048, 0.03, 35), (4096, 0.01, 36)])
+def test_pivot_rules_rows_in_l2(ctx, mce, mode, n, p, seed):
+    # above 1024 vertices the rows do not fit in shared memory and the
+    # kernels read them from L2: every pivot rule's tree must still be exact
+    uv = synth.gnp(n, p, seed)
+    expect_equal(run_host(ctx, mce, n, uv, pivot=mode), n, uv, mode=mode, what=f"{mode} G({n},{p})")
+
+
 SHAPES = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4),
           (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4)]
 
@@ -187,12 +196,18 @@ def test_invalid_inputs(ctx, mce):
 
 
 def test_timeout_is_reported_and_context_survives(ctx, mce):
-    n, uv = 36, synth.moon_moser(12)
+    # Moon-Moser on 45 vertices runs for milliseconds; with a 1 us wait
+    # budget the device-side bound (10 x timeout_ns since the launch, checked
+    # by every block's refresh of the device-wide queue, which idle warps do
+    # from the first microseconds) must fire: the search stops with
+    # MCE_ETIMEOUT, and the same context then runs the graph to completion.
+    n, uv = 45, synth.moon_moser(15)
     g = ctx.load_edges(n, uv)
-    r = g.enumerate(mce.options(timeout_ns=1), raise_on_error=False)
-    assert r["rc"] in (mce.MCE_ETIMEOUT, mce.MCE_OK)
+    for _ in range(2):
+        r = g.enumerate(mce.options(timeout_ns=1000), raise_on_error=False)
+        assert r["rc"] == mce.MCE_ETIMEOUT
     ok = g.enumerate()
-    assert ok["count"] == 3 ** 12
+    assert ok["rc"] == 0 and ok["count"] == 3 ** 15
     g.free()
 
 
@@ -267,4 +282,18 @@ def test_full_size_workload(ctx, mce, name):
     hist = {str(k): int(v) for k, v in enumerate(got["hist"]) if v}
     assert hist == gold["hist"]
     t = gold["greedy"]
+    assert (got["nodes"], got["internal"], got["dead_ends"]) == (t["nodes"], t["internal"], t["dead_ends"])
+
+
+@pytest.mark.parametrize("mode", ["tx", "tomita", "nx"])
+def test_full_size_pivot_rules(ctx, mce, mode):
+    # G(1000, 0.3) seed 1 under GreedyBBTX, TomitaBB and GreedyBBNX (NX has
+    # TX's tree): counters against the oracle's stored trees
+    gold = _golden().get("gnp_1000_0.3_s1")
+    if gold is None:
+        pytest.skip("expected values not generated")
+    n, uv = WORKLOADS["gnp_1000_0.3_s1"]()
+    got = run_host(ctx, mce, n, uv, pivot=mode)
+    assert (got["count"], got["hash"]) == (gold["count"], gold["hash"])
+    t = gold["tx" if mode == "nx" else mode]
     assert (got["nodes"], got["internal"], got["dead_ends"]) == (t["nodes"], t["internal"], t["dead_ends"])

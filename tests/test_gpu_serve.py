@@ -2,6 +2,8 @@
 while others run give exactly their alone results and the oracle's."""
 from __future__ import annotations
 
+import os
+import sys
 import time
 
 import numpy as np
@@ -9,6 +11,8 @@ import pytest
 
 import oracle
 import synth
+
+sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
 
 pytestmark = pytest.mark.gpu
 
@@ -93,3 +97,42 @@ def test_queued_requests_share_launches(mce, pivot):
     for g in graphs:
         g.free()
     ctx.close()
+
+
+def _gen_served_rows(r):
+    g = synth.served_graph(r)
+    return g.n, synth.to_bitset(g.n, g.uv)
+
+
+def test_served_workload_matches_oracle(mce):
+    """The first 2000 requests of the served workload (capped G(n, p), n
+    log-uniform in [64, 2048]) submitted as a Poisson stream while earlier
+    ones run, each against the oracle's stored count, hash, histogram and
+    GreedyBB tree (tests/golden/served2000_results.txt)."""
+    import multiprocessing as mp
+    import make_workload_golden as mk
+    gold = mk.load("served")
+    assert len(gold) == 2000
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        specs = pool.map(_gen_served_rows, range(2000), chunksize=16)
+    ctx = mce.Context(0)
+    graphs = [ctx.load_bitset(n, rows) for n, rows in specs]
+    gaps = np.diff(synth.served_arrivals(2000, 4000.0), prepend=0.0)
+    t0 = time.perf_counter()
+    due = np.cumsum(gaps)
+    tickets = []
+    for g, at in zip(graphs, due):           # arrive at about 4000 requests/s
+        while time.perf_counter() - t0 < at:
+            pass
+        tickets.append(ctx.submit(g))
+    got = [ctx.wait(t, timeout_ns=120_000_000_000) for t in tickets]
+    bad = []
+    for g, r in zip(gold, got):
+        hist = {k: int(v) for k, v in enumerate(r["hist"]) if v}
+        if (r["rc"], r["count"], r["hash"], r["nodes"], r["internal"], r["dead_ends"], hist) != \
+                (0, g["count"], g["hash"], g["nodes"], g["internal"], g["dead_ends"], g["hist"]):
+            bad.append(g["index"])
+    for g in graphs:
+        g.free()
+    ctx.close()
+    assert not bad, bad[:20]

@@ -1,14 +1,14 @@
 """The no-allocation entry point (mce_enumerate_device_static).
 
 Some callers may not allocate device memory at all: a plug-in whose host
-framework owns every device allocation, a request path that must not
-allocate per call, code running inside someone else's stream capture.  For
-them the library keeps one fixed scratch area per GPU and this entry point
-uses it instead of a caller-provided scratch buffer.  The test calls it
-twice in a row through the C ABI and compares every output word with the
-regular entry point's (the results are exact integers, so equality is the
-tolerance).  This file is collected last so that a stop-at-first-failure run
-has already run every other test.
+framework owns every device allocation, or a request path that must not
+allocate per call.  For them the library keeps one fixed scratch area per GPU
+and this entry point uses it instead of a caller-provided scratch buffer.
+The test calls it twice in a row through the C ABI and compares every output
+word with the regular entry point's (the results are exact integers, so
+equality is the tolerance), and checks that a call leaves the device's free
+memory unchanged.  This file is collected last so that a stop-at-first-failure
+run has already run every other test.
 """
 from __future__ import annotations
 
@@ -31,7 +31,7 @@ def mce():
     return m
 
 
-@pytest.mark.parametrize("n,p,seed", [(100, 0.5, 0), (45, 0.9, 3), (700, 0.3, 2), (2048, 0.05, 5)])
+@pytest.mark.parametrize("n,p,seed", [(100, 0.5, 0), (45, 0.9, 3), (700, 0.3, 2), (2048, 0.05, 5), (4096, 0.01, 6)])
 def test_static_scratch_matches_regular_entry_point(mce, n, p, seed):
     import torch
     dev = torch.device("cuda:0")
@@ -48,10 +48,14 @@ def test_static_scratch_matches_regular_entry_point(mce, n, p, seed):
     torch.cuda.synchronize()
     want = mce.decode_out(ref, n)
     assert want["status"] == 0
-    for _ in range(2):                       # the area keeps the previous call's contents
+    for call in range(2):                    # the area keeps the previous call's contents
         out = torch.full((mce.MCE_OUT_WORDS(n),), -1, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert mce.mce_enumerate_device_static(n, W, rows, o, out, s) == mce.MCE_OK
         torch.cuda.synchronize()
+        if call == 1:                        # the first call may load device code
+            assert torch.cuda.mem_get_info()[0] == free0
         got = mce.decode_out(out, n)
         for key in ("status", "count", "nodes", "internal", "dead_ends", "hash", "max_size"):
             assert got[key] == want[key], key
