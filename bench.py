@@ -849,7 +849,8 @@ def run_ours(args):
     count, nodes = res["count"], res["nodes"]
     value = job_rate(world, args.steps, count, total_ms)
     gold = golden()
-    check = {"status": res["status"], "count": count, "nodes": nodes, "hash": res["hash"]}
+    check = {"status": res["status"], "count": count, "nodes": nodes, "hash": res["hash"],
+             "lane_tasks": res["lane_tasks"], "steals": res["steals"], "donations": res["donations"]}
     if gold:
         check["matches_oracle"] = (count == gold["count"] and res["hash"] == gold["hash"]
                                    and nodes == gold["greedy"]["nodes"] and r2["count"] == gold["count"])

@@ -169,6 +169,9 @@ typedef struct {
 #define MCE_OUT_GPUSH     12   /* frames published to the device-wide queue  */
 #define MCE_OUT_GTRY      13   /* attempts to take a frame from it           */
 #define MCE_OUT_CAS_FAIL  14   /* lost compare-and-swap races on its tickets */
+#define MCE_OUT_LANE_TASKS 15  /* subtrees handed to single lanes (frames
+                                  whose P u X has at most 32 vertices,
+                                  searched with 32-bit local sets)          */
 #define MCE_OUT_HIST       16
 #define MCE_OUT_WORDS(n)   (MCE_OUT_HIST + (uint64_t)(n) + 1)
 
@@ -411,8 +414,9 @@ const char *mce_strerror(int code);
  * caller-owned, zeroed by the caller) is split evenly between the launch's
  * blocks; each block appends 16-byte records whenever it refreshes its view
  * of the device-wide queue (about every 2 us while it runs):
- *   uint64 globaltimer ns, uint16 busy groups of the block, uint16 frames in
- *   the block ring, uint16 frames in the device-wide queue (saturating),
+ *   uint64 globaltimer ns, uint16 busy groups of the block, uint16 lanes of
+ *   the block holding a lane-tier subproblem (frames whose P u X has at most
+ *   32 vertices), uint16 frames in the device-wide queue (saturating),
  *   uint16 starving blocks (saturating).
  * Records past a block's share are dropped. */
 int mce_trace_enable(void *d_buf, uint64_t bytes);

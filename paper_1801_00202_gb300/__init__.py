@@ -35,7 +35,7 @@ MCE_ORDER_IDENTITY, MCE_LIST, MCE_LIST_SORTED, MCE_AUTOTUNE, MCE_OUTER = 0x1, 0x
 MCE_OUT_COUNT, MCE_OUT_NODES, MCE_OUT_INTERNAL, MCE_OUT_DEAD_ENDS = 0, 1, 2, 3
 MCE_OUT_HASH, MCE_OUT_STATUS, MCE_OUT_MAX_SIZE, MCE_OUT_DONATIONS = 4, 5, 6, 7
 MCE_OUT_STEALS, MCE_OUT_GLOBAL, MCE_OUT_BUSY_NS, MCE_OUT_GROUPS = 8, 9, 10, 11
-MCE_OUT_GPUSH, MCE_OUT_GTRY, MCE_OUT_CAS_FAIL = 12, 13, 14
+MCE_OUT_GPUSH, MCE_OUT_GTRY, MCE_OUT_CAS_FAIL, MCE_OUT_LANE_TASKS = 12, 13, 14, 15
 MCE_OUT_HIST = 16
 
 
@@ -248,7 +248,7 @@ def decode_out(out, n: int) -> dict:
             "steals": int(a[MCE_OUT_STEALS]), "global_steals": int(a[MCE_OUT_GLOBAL]),
             "busy_ns": int(a[MCE_OUT_BUSY_NS]), "groups": int(a[MCE_OUT_GROUPS]),
             "global_pushes": int(a[MCE_OUT_GPUSH]), "global_tries": int(a[MCE_OUT_GTRY]),
-            "cas_fails": int(a[MCE_OUT_CAS_FAIL]),
+            "cas_fails": int(a[MCE_OUT_CAS_FAIL]), "lane_tasks": int(a[MCE_OUT_LANE_TASKS]),
             "hist": a[MCE_OUT_HIST:MCE_OUT_HIST + n + 1].copy()}
 
 

@@ -36,6 +36,8 @@ struct Config {
     uint32_t total_groups = 0;
     int pivot = 0;
     bool list = false;  // frames carry R (clique listing)
+    uint32_t t2_offset = 0, t2_levels = 0, t2_max_p = 0;  // lane tier (t2_max_p 0: off)
+    bool seed = false;  // start from the root's children
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -156,13 +158,41 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return MCE_ECUDA;
     const size_t limit = (size_t)optin - 1024;  // static shared memory + slack
 
-    c.smem = c.wp <= 32 && search_smem(n, c.wp, true, c.list) <= limit;
+    c.threads = o.threads_per_block ? o.threads_per_block : kMaxThreads;
+    if (c.threads % 32 || c.threads > kMaxThreads) return MCE_EINVAL;
+
+    // The lane tier (counting kernels, groups of two or more lanes; not in
+    // the served form, whose blocks stay small so that requests share SMs)
+    // needs t2_warp_bytes per warp.  Rows stay in shared memory when they fit
+    // beside it; otherwise they are read from L2, or, with t2_smem_rows, the
+    // block gets fewer warps so that they fit.
+    const Tuning tu = default_tuning();
+    const bool t2 = !c.list && G >= 2 && tu.t2_p != 0 && stack_cap == ~(size_t)0;
+    const size_t t2w = t2 ? t2_warp_bytes(tu.t2_levels) : 0;
+    auto fits = [&](bool rows_smem, unsigned threads) {
+        return round_up(search_smem(n, c.wp, rows_smem, c.list), 16) + (size_t)(threads / 32) * t2w <= limit;
+    };
+    c.smem = c.wp <= 32 && fits(true, c.threads);
+    if (!c.smem && t2 && tu.t2_smem_rows && c.wp <= 32 && !o.threads_per_block) {
+        for (unsigned th = c.threads - 64; th >= 128 && !c.smem; th -= 64)
+            if (fits(true, th)) {
+                c.threads = th;
+                c.smem = true;
+            }
+    }
+    if (t2 && !fits(c.smem, c.threads) && !o.threads_per_block)
+        while (c.threads > 128 && !fits(c.smem, c.threads)) c.threads -= 64;
+    const bool t2_on = t2 && fits(c.smem, c.threads);
     if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode, c.list);
     if (search_smem(n, c.wp, c.smem, c.list) > limit) return MCE_EINVAL;
 
-    c.threads = o.threads_per_block ? o.threads_per_block : kMaxThreads;
-    if (c.threads % 32 || c.threads > kMaxThreads) return MCE_EINVAL;
-    const size_t base = search_smem(n, c.wp, c.smem, c.list);
+    size_t base = search_smem(n, c.wp, c.smem, c.list);
+    if (t2_on) {
+        c.t2_offset = (uint32_t)round_up(base, 16);
+        c.t2_levels = tu.t2_levels;
+        c.t2_max_p = tu.t2_p;
+        base = c.t2_offset + (size_t)(c.threads / 32) * t2w;
+    }
     const size_t cap = stack_cap < limit - base ? base + stack_cap : limit;
     plan_stack_for((uint32_t)base, c.G, c.K, c.threads, cap, c.stack_levels, c.stack_offset, c.smem_bytes);
     if (o.blocks) {
@@ -175,6 +205,8 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     }
     c.total_groups = c.blocks * (c.threads / 32) * (32 / G);
     c.qcap = next_pow2(std::max<uint64_t>(1024, 4ull * c.total_groups + 256));
+    c.seed = tu.seed != 0;
+    if (c.seed) c.qcap = std::max<uint32_t>(c.qcap, next_pow2(2ull * n + 256));  // every root child queued at once
     if (o.queue_log2) c.qcap = std::max<uint32_t>(c.qcap, 1u << o.queue_log2);
     c.fs = (uint32_t)frame_words(c.wp, c.list);
     return MCE_OK;
@@ -214,14 +246,14 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 0u, 1u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
                 char key[32] = {0};
                 unsigned val = 0;
                 int used = 0;
-                if (std::sscanf(p, "%31[a-z_]=%u%n", key, &val, &used) != 2) break;
+                if (std::sscanf(p, "%31[a-z0-9_]=%u%n", key, &val, &used) != 2) break;
                 if (!std::strcmp(key, "share_local")) d.share_local = val;
                 else if (!std::strcmp(key, "share_global")) d.share_global = val;
                 else if (!std::strcmp(key, "local_check") && val) d.local_check = pow2_ceil(val);
@@ -231,6 +263,10 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "pop_tries") && val) d.pop_tries = val;
                 else if (!std::strcmp(key, "share_tail") && val) d.share_tail = val;
                 else if (!std::strcmp(key, "idle_sleep_ns") && val) d.idle_sleep_ns = val;
+                else if (!std::strcmp(key, "t2_p")) d.t2_p = std::min(val, 32u);
+                else if (!std::strcmp(key, "t2_levels")) d.t2_levels = std::min(val, 31u);
+                else if (!std::strcmp(key, "t2_smem_rows")) d.t2_smem_rows = val;
+                else if (!std::strcmp(key, "seed")) d.seed = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -278,6 +314,10 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
     p.part = nullptr;
     p.part_k = 0;
     p.count_root = 1;
+    p.t2_offset = c.t2_offset;
+    p.t2_levels = c.t2_levels;
+    p.t2_max_p = c.t2_max_p;
+    p.seed_children = c.seed ? 1u : 0u;
     return p;
 }
 

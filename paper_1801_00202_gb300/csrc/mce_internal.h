@@ -48,8 +48,14 @@ struct LocalHdr {
     unsigned g_head, g_tail, g_starving, g_abort;
     unsigned long long stamp;
     unsigned trace_n;     // timeline records written by this block
-    unsigned pad;
+    unsigned t2_busy;     // lanes of the block holding a lane-tier subproblem
+    // work-distribution diagnostics of the block (rare events, shared-memory
+    // atomics; added to the result array once the block is done)
+    unsigned long long diag[8];
 };
+// Indices of LocalHdr::diag and the result words they are added to.
+enum DiagIdx { kDiagDonations = 0, kDiagSteals, kDiagGlobal, kDiagBusyNs, kDiagGpush, kDiagGtry, kDiagCasFail,
+               kDiagLaneTasks, kDiagCount };
 __host__ __device__ inline size_t frame_words(uint32_t wp, bool list = false)
 {
     return (8 + (list ? 3 : 2) * (size_t)wp + 3) / 4 * 4;
@@ -86,7 +92,23 @@ struct Tuning {
     uint32_t pop_tries;     // ticket attempts of one take from the device-wide ring
     uint32_t share_tail;    // smallest |P| shared once half the groups/blocks are idle
     uint32_t idle_sleep_ns; // longest back-off of an idle warp that is not polling
+    uint32_t t2_p;          // lane tier: largest |P| of a subproblem handed to one lane (0: off)
+    uint32_t t2_levels;     // lane tier: explicit-stack levels per lane in shared memory
+    uint32_t t2_smem_rows;  // lane tier on: keep the rows in shared memory (fewer warps) when 1
+    uint32_t seed;          // start from every root child as its own queued frame (1) or the root (0)
 };
+
+// The lane tier (second search tier): a frame whose P u X has at most 32
+// vertices is relabelled 0..u-1 in order and searched by one lane with 32-bit
+// sets.  Per warp in shared memory: the 32 lanes' local adjacency rows
+// A[row][lane] (u32), the positions of their local vertices pos[v][lane]
+// (u16), and t2_levels explicit-stack levels of six words per lane
+// [level][field][lane] (P, X, L, |R|, S low, S high).
+constexpr int kT2Fields = 6;
+__host__ __device__ inline size_t t2_warp_bytes(uint32_t levels)
+{
+    return 32 * 32 * 4 + 32 * 32 * 2 + (size_t)levels * kT2Fields * 32 * 4;
+}
 
 struct SearchParams {
     uint32_t n;             // vertices
@@ -118,6 +140,13 @@ struct SearchParams {
     const uint32_t *part;
     uint32_t part_k;
     uint32_t count_root;
+    // lane tier: byte offset of its shared-memory region (t2_warp_bytes per
+    // warp), stack levels kept there, and the largest |P| handed to a lane
+    // (0: the tier is off)
+    uint32_t t2_offset, t2_levels, t2_max_p;
+    // start from the root's children, each its own queued frame, instead of
+    // the root frame (the root is still counted once)
+    uint32_t seed_children;
 };
 
 // One graph of a batch (device table entry; pointers into library memory).
@@ -172,6 +201,7 @@ struct BatchParams {
     uint32_t split_min_p, split_target;
     uint32_t stack_smem_levels, stack_offset;
     Tuning tune;
+    uint32_t t2_offset, t2_levels, t2_max_p;  // lane tier (as in SearchParams)
 };
 
 // Per-block queue region of the batched search: [Ctl | seq | frames]
@@ -249,6 +279,9 @@ cudaError_t launch_root_children(const uint32_t *rows, uint32_t n, uint32_t wp, 
 // Queue frame j (< prm.part_k) = child prm.part[j] (after search_init_kernel
 // reserved the slots); an index beyond |L| or out of order sets MCE_EINVAL.
 cudaError_t launch_part_frames(const SearchParams &prm, const unsigned *root_pivot, cudaStream_t s);
+// Queue every root child as its own frame (after search_init_kernel left the
+// queue empty): frame t in slot t, tail = pending = |L|.  prm.qcap >= n.
+cudaError_t launch_seed_children(const SearchParams &prm, const unsigned *root_pivot, cudaStream_t s);
 // TomitaBB's root pivot (the earliest vertex of maximum degree) to *dst.
 cudaError_t launch_root_degree_pivot(const uint32_t *rows, uint32_t n, uint32_t wp, unsigned *dst, cudaStream_t s);
 

@@ -151,7 +151,7 @@ __device__ __forceinline__ void set_status(uint64_t *out, Ctl *ctl, int code)
 // frame for consumer `ticket`).
 
 __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
-                                               uint64_t &fails)
+                                               unsigned long long *fails)
 {
     unsigned pos = ld_relaxed(&ctl->tail);
     for (unsigned t = 0; t < kCasTries; ++t) {
@@ -160,7 +160,7 @@ __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned
         if (dif == 0) {
             unsigned prev = atomicCAS(&ctl->tail, pos, pos + 1);
             if (prev == pos) { ticket = pos; return true; }
-            ++fails;
+            atomicAdd(fails, 1ull);
             pos = prev;
         } else if (dif < 0) {
             return false;  // full
@@ -172,7 +172,7 @@ __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned
 }
 
 __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
-                                              uint64_t &fails, unsigned tries = kCasTries)
+                                              unsigned long long *fails, unsigned tries = kCasTries)
 {
     unsigned pos = ld_relaxed(&ctl->head);
     for (unsigned t = 0; t < tries; ++t) {
@@ -181,7 +181,7 @@ __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned 
         if (dif == 0) {
             unsigned prev = atomicCAS(&ctl->head, pos, pos + 1);
             if (prev == pos) { ticket = pos; return true; }
-            ++fails;
+            atomicAdd(fails, 1ull);
             pos = prev;
         } else if (dif < 0) {
             return false;  // empty
@@ -196,7 +196,7 @@ __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned 
 // advance: consumer tickets first .. first + k - 1.  Returns k (0 when the
 // ring is empty or the tries ran out).
 __device__ __forceinline__ unsigned q_reserve_pop_many(Ctl *ctl, unsigned *seq, unsigned mask, unsigned want,
-                                                       unsigned &first, uint64_t &fails, unsigned tries)
+                                                       unsigned &first, unsigned long long *fails, unsigned tries)
 {
     unsigned pos = ld_relaxed(&ctl->head);
     for (unsigned t = 0; t < tries; ++t) {
@@ -213,7 +213,7 @@ __device__ __forceinline__ unsigned q_reserve_pop_many(Ctl *ctl, unsigned *seq, 
             first = pos;
             return k;
         }
-        ++fails;
+        atomicAdd(fails, 1ull);
         pos = prev;
     }
     return 0u;
@@ -467,15 +467,19 @@ __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned grou
         q.h->g_abort = 0u;
         q.h->stamp = 0ull;
         q.h->trace_n = 0u;
+        q.h->t2_busy = 0u;
+        for (int i = 0; i < kDiagCount; ++i) q.h->diag[i] = 0ull;
     }
 }
 
-// Per-warp result counters (meaningful in group leaders; summed at the end;
-// nodes is formed at the flush as leaves + dead ends + internal nodes).
+// Per-lane result counters (summed over the warp at the end; nodes is formed
+// at the flush as leaves + dead ends + internal nodes).  The block's
+// work-distribution diagnostics live in shared memory (diag).
 struct Counters {
-    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0, don = 0, steals = 0, gsteals = 0, busy = 0;
-    uint64_t gpush = 0, gtry = 0, cas_fail = 0;  // device-wide ring diagnostics
+    uint64_t cnt = 0, nodes = 0, intl = 0, dead = 0, hash = 0;
     unsigned max = 0;
+    unsigned long long *diag = nullptr;
+    __device__ __forceinline__ void note(int i, unsigned long long v = 1ull) const { atomicAdd(diag + i, v); }
 };
 
 // ---------------------------------------------------------------------------
@@ -545,8 +549,8 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
             if (!got) atomicSub(&lq.h->bwork, 1u);
         } else {
             atomicAdd(&prm.ctl->pending, 1u);
-            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket, cn.cas_fail) ? 1u : 0u;
-            cn.gpush += got;
+            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket, cn.diag + kDiagCasFail) ? 1u : 0u;
+            if (got) cn.note(kDiagGpush);
             if (!got) atomicSub(&prm.ctl->pending, 1u);
         }
     }
@@ -596,7 +600,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
         } else {
             st_release(&prm.seq[ticket & (prm.qcap - 1u)], ticket + 1u);
         }
-        ++cn.don;
+        cn.note(kDiagDonations);
     }
     whole = give >= c;
     return got != 0u;
@@ -614,13 +618,6 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         c.intl += __shfl_xor_sync(FULL, c.intl, o);
         c.dead += __shfl_xor_sync(FULL, c.dead, o);
         c.hash += __shfl_xor_sync(FULL, c.hash, o);
-        c.don += __shfl_xor_sync(FULL, c.don, o);
-        c.steals += __shfl_xor_sync(FULL, c.steals, o);
-        c.gsteals += __shfl_xor_sync(FULL, c.gsteals, o);
-        c.busy += __shfl_xor_sync(FULL, c.busy, o);
-        c.gpush += __shfl_xor_sync(FULL, c.gpush, o);
-        c.gtry += __shfl_xor_sync(FULL, c.gtry, o);
-        c.cas_fail += __shfl_xor_sync(FULL, c.cas_fail, o);
         c.max = max(c.max, __shfl_xor_sync(FULL, c.max, o));
     }
     if ((threadIdx.x & 31u) == 0) {
@@ -630,15 +627,20 @@ __device__ __forceinline__ void flush_counters(Counters &c, uint64_t *out)
         if (c.intl) atomicAdd(o + MCE_OUT_INTERNAL, c.intl);
         if (c.dead) atomicAdd(o + MCE_OUT_DEAD_ENDS, c.dead);
         if (c.hash) atomicAdd(o + MCE_OUT_HASH, c.hash);
-        if (c.don) atomicAdd(o + MCE_OUT_DONATIONS, c.don);
-        if (c.steals) atomicAdd(o + MCE_OUT_STEALS, c.steals);
-        if (c.gsteals) atomicAdd(o + MCE_OUT_GLOBAL, c.gsteals);
-        if (c.busy) atomicAdd(o + MCE_OUT_BUSY_NS, c.busy);
-        if (c.gpush) atomicAdd(o + MCE_OUT_GPUSH, c.gpush);
-        if (c.gtry) atomicAdd(o + MCE_OUT_GTRY, c.gtry);
-        if (c.cas_fail) atomicAdd(o + MCE_OUT_CAS_FAIL, c.cas_fail);
         if (c.max) atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)c.max);
     }
+}
+
+// The block's diagnostics to out[] (one thread, after the block's warps are
+// done).
+__device__ __forceinline__ void flush_diag(const unsigned long long *diag, uint64_t *out)
+{
+    unsigned long long *o = reinterpret_cast<unsigned long long *>(out);
+    const int word[kDiagCount] = {MCE_OUT_DONATIONS, MCE_OUT_STEALS,   MCE_OUT_GLOBAL,    MCE_OUT_BUSY_NS,
+                                  MCE_OUT_GPUSH,     MCE_OUT_GTRY,     MCE_OUT_CAS_FAIL,  MCE_OUT_LANE_TASKS};
+#pragma unroll
+    for (int i = 0; i < kDiagCount; ++i)
+        if (diag[i]) atomicAdd(o + word[i], diag[i]);
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
@@ -841,8 +843,8 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
     unsigned ticket = 0, got = 0;
     if (pred && g.leader()) {
         atomicAdd(&prm.ctl->pending, 1u);
-        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket, cn.cas_fail) ? 1u : 0u;
-        cn.gpush += got;
+        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket, cn.diag + kDiagCasFail) ? 1u : 0u;
+        if (got) cn.note(kDiagGpush);
         if (!got) atomicSub(&prm.ctl->pending, 1u);
     }
     got = g.from_leader(got);
@@ -868,6 +870,134 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
     return got != 0u;
 }
 
+// ---------------------------------------------------------------------------
+// The lane tier.  Most nodes of the search tree lie where few vertices are
+// left: once a frame's P u X has at most 32 vertices, nothing outside that
+// set can ever enter a descendant's P or X (Alg. 4 only intersects them with
+// rows of vertices of P).  Such a frame is compressed: U = P u X in
+// increasing position is relabelled 0..u-1 -- order-preserving, so "first in
+// the order" is still the lowest set bit and every pivot rule (first of X or
+// P; the TX / TomitaBB argmax with ties to the earliest) picks the same
+// vertex -- its induced adjacency becomes u rows of 32 bits, and one lane
+// runs Alg. 4 on it alone with single-word sets, next to 31 other lanes doing
+// the same on their own subproblems.  The tree, the leaves and the hash terms
+// (through the positions of the local vertices) are exactly those of the
+// group search.
+
+struct T2Lane {
+    uint32_t P = 0, X = 0, L = 0, rs = 0;  // local sets of the current frame, |R|
+    uint64_t S = 0;                        // S(R)
+    int d = 0;                             // explicit-stack depth
+    bool busy = false;
+};
+
+struct T2Warp {
+    uint32_t *A;    // [32 local rows][32 lanes]
+    uint16_t *pos;  // [32 local vertices][32 lanes]: position in the order
+    uint32_t *stk;  // [levels][kT2Fields][32 lanes]
+    int levels;
+};
+
+// One node of every busy lane's subproblem: the child v = first of L of the
+// lane's current frame (the same step as the group search's section C, on
+// 32-bit sets).  Divergent by design: no warp collectives inside.
+template <int PIVOT>
+__device__ __forceinline__ void t2_step(T2Lane &t, const T2Warp &m, unsigned lane, const uint64_t *hv,
+                                        const uint64_t *hk, uint32_t *hist, uint64_t *out, uint32_t pivot_mode,
+                                        uint32_t (&spill)[32][kT2Fields], Counters &cn, unsigned *busy_lanes)
+{
+    if (!t.busy) return;
+    const int v = __ffs(t.L) - 1;
+    t.L &= t.L - 1u;
+    const uint32_t *A = m.A + lane;
+    const uint32_t a = A[v * 32];
+    const uint32_t Pc = t.P & a, Xc = t.X & a;  // P n N(v), X n N(v)
+    t.P &= ~(1u << v);                           // P <- P \ {v}
+    t.X |= 1u << v;                              // X <- X u {v}
+    const uint64_t Sc = t.S + hv[m.pos[v * 32 + lane]];
+    const unsigned k = t.rs + 1u;
+    if (Pc == 0u) {
+        if (Xc == 0u) {  // P u X empty: R u {v} is a maximal clique
+            ++cn.cnt;
+            cn.hash += mix64(Sc ^ hk[k]);
+            cn.max = k > cn.max ? k : cn.max;
+            const unsigned old = atomicAdd(&hist[k], 1u);
+            if (old == 0xffffffffu)
+                atomicAdd(reinterpret_cast<unsigned long long *>(out + MCE_OUT_HIST + k), 1ull << 32);
+        } else {
+            ++cn.dead;
+        }
+    } else {
+        ++cn.intl;
+    }
+    uint32_t Lc = 0u;
+    if (Pc != 0u) {
+        int p;
+        if (PIVOT == MCE_PIVOT_GREEDY) {
+            p = __ffs(Xc != 0u ? Xc : Pc) - 1;
+        } else {
+            // argmax |P' n N(u)| over X' (TX, NX) or P' u X' (TomitaBB),
+            // candidates in increasing position with '>' keeping the earliest
+            uint32_t cand = (PIVOT == MCE_PIVOT_GREEDY_TX) ? Xc : (Pc | Xc);
+            p = __ffs(Pc) - 1;  // TX with X' empty: first of P'
+            int best = -1;
+            const int all = __popc(Pc);
+            const bool nx = PIVOT == MCE_PIVOT_GREEDY_TX && pivot_mode == MCE_PIVOT_GREEDY_NX;
+            while (cand) {
+                const int u = __ffs(cand) - 1;
+                cand &= cand - 1u;
+                const int c = __popc(Pc & A[u * 32]);
+                if (c > best) {
+                    best = c;
+                    p = u;
+                }
+                if (nx && best == all) break;  // Naude's early exit: nothing later can beat it
+            }
+        }
+        Lc = Pc & ~A[p * 32];  // L' = P' \ N(p)
+    }
+    if (Lc != 0u) {
+        if (t.L != 0u) {  // the frame keeps children: push it
+            const uint32_t f[kT2Fields] = {t.P, t.X, t.L, t.rs, (uint32_t)t.S, (uint32_t)(t.S >> 32)};
+            if (t.d < m.levels) {
+                uint32_t *w = m.stk + (size_t)t.d * kT2Fields * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < kT2Fields; ++i) w[i * 32] = f[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < kT2Fields; ++i) spill[t.d][i] = f[i];
+            }
+            ++t.d;
+        }
+        t.P = Pc;
+        t.X = Xc;
+        t.L = Lc;
+        t.rs = k;
+        t.S = Sc;
+    } else if (t.L == 0u) {  // the frame is exhausted: back to its parent
+        if (t.d == 0) {
+            t.busy = false;
+            atomicSub(busy_lanes, 1u);
+        } else {
+            --t.d;
+            uint32_t f[kT2Fields];
+            if (t.d < m.levels) {
+                const uint32_t *w = m.stk + (size_t)t.d * kT2Fields * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < kT2Fields; ++i) f[i] = w[i * 32];
+            } else {
+#pragma unroll
+                for (int i = 0; i < kT2Fields; ++i) f[i] = spill[t.d][i];
+            }
+            t.P = f[0];
+            t.X = f[1];
+            t.L = f[2];
+            t.rs = f[3];
+            t.S = (uint64_t)f[4] | ((uint64_t)f[5] << 32);
+        }
+    }
+}
+
 // The search proper: the groups of this warp expand frames until the search
 // is over or aborts.  Work moves at two levels: idle groups take frames from
 // the block's shared-memory ring, which busy groups of the block refill by
@@ -880,10 +1010,15 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
 template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint32_t *rows, const uint64_t *hv,
                                             const uint64_t *hk, uint32_t *hist, const LocalQ &lq, const Thresholds th,
-                                            uint32_t *stack_smem, int stack_smem_levels, Counters &cn)
+                                            uint32_t *stack_smem, int stack_smem_levels, unsigned char *t2_smem,
+                                            Counters &cn)
 {
     using Gp = Grp<G, K>;
     constexpr int WP = G * K;
+    // the lane tier serves the counting kernels of groups of two or more
+    // lanes (one-lane groups already search with one or two words per lane)
+    constexpr bool T2 = !LIST && G >= 2;
+    constexpr unsigned GPW = 32u / G;  // groups per warp
     const uint32_t n = prm.n;
     Ctl *ctl = prm.ctl;
     Gp g;
@@ -912,6 +1047,20 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     stk.sm = stack_smem + (size_t)(threadIdx.x >> 5) * (size_t)stack_smem_levels * Stk::LW * 32;
     stk.ln = g.lane;
     stk.lw = stack_local;
+
+    // lane tier: this lane's subproblem and the warp's region
+    T2Lane t2;
+    T2Warp t2m;
+    uint32_t t2_spill[32][kT2Fields];
+    const unsigned t2p = T2 ? min(prm.t2_max_p, th.share_local) : 0u;
+    {
+        unsigned char *wb = t2_smem + (size_t)(threadIdx.x >> 5) * t2_warp_bytes(prm.t2_levels);
+        t2m.A = reinterpret_cast<uint32_t *>(wb);
+        t2m.pos = reinterpret_cast<uint16_t *>(wb + 32 * 32 * 4);
+        t2m.stk = reinterpret_cast<uint32_t *>(wb + 32 * 32 * 4 + 32 * 32 * 2);
+        t2m.levels = (int)prm.t2_levels;
+    }
+    unsigned t2it = 0;
 
     uint64_t quiet_since = 0;
     const uint64_t t_start = global_ns();
@@ -1073,7 +1222,116 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         }
     };
 
-    for (unsigned it = 0;; ++it) {
+    // Hand the child frames (Pc, Xc, Lc, |R| = rs1, S = Sc) of the groups
+    // with `comp` to free lanes of this warp as lane-tier subproblems (the
+    // first groups in lane order, as many as lanes are free).  Per group: the
+    // group's lanes list U = Pc u Xc in order into the slot's position column
+    // and form the local P, X, L words; then the whole warp builds the local
+    // rows, one ballot per row (lane i tests whether U[i] is adjacent to
+    // U[j]).  Warp-uniform call; true in the groups whose frame was taken.
+    auto t2_take = [&](bool comp, const uint32_t (&Pc)[K], const uint32_t (&Xc)[K], const uint32_t (&Lc)[K],
+                       unsigned rs1, uint64_t Sc) -> bool {
+        const unsigned freem = ~__ballot_sync(FULL, t2.busy);
+        const unsigned leads = __ballot_sync(FULL, comp && g.leader());
+        const unsigned rank = (unsigned)__popc(leads & ((1u << g.gbase) - 1u));
+        const bool ok = comp && rank < (unsigned)__popc(freem);
+        const unsigned okl = __ballot_sync(FULL, ok && g.leader());
+        if (okl == 0u) return false;
+        unsigned f = freem;
+        for (unsigned r = 0; r < rank && f; ++r) f &= f - 1u;
+        const unsigned slot = (ok && f) ? (unsigned)(__ffs(f) - 1) : 0u;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) cnt += ok ? __popc(Pc[k] | Xc[k]) : 0;
+        const int off = g.excl_scan(cnt);
+        const int u_grp = g.sum(cnt);
+        uint32_t lp = 0u, lx = 0u, ll = 0u;
+        if (ok) {
+            unsigned i = (unsigned)off;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                uint32_t w = Pc[k] | Xc[k];
+                while (w) {
+                    const unsigned b = (unsigned)(__ffs(w) - 1);
+                    w &= w - 1u;
+                    t2m.pos[i * 32 + slot] = (uint16_t)((g.gl * K + k) * 32u + b);
+                    lp |= ((Pc[k] >> b) & 1u) << i;
+                    lx |= ((Xc[k] >> b) & 1u) << i;
+                    ll |= ((Lc[k] >> b) & 1u) << i;
+                    ++i;
+                }
+            }
+        }
+        if (G > 1) {
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                lp |= __shfl_xor_sync(FULL, lp, o);
+                lx |= __shfl_xor_sync(FULL, lx, o);
+                ll |= __shfl_xor_sync(FULL, ll, o);
+            }
+        }
+        __syncwarp();
+        unsigned todo = okl;
+        while (todo) {
+            const int gb = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const unsigned s = __shfl_sync(FULL, slot, gb);
+            const unsigned u = (unsigned)__shfl_sync(FULL, u_grp, gb);
+            const uint32_t P0 = __shfl_sync(FULL, lp, gb), X0 = __shfl_sync(FULL, lx, gb);
+            const uint32_t L0 = __shfl_sync(FULL, ll, gb), r0 = __shfl_sync(FULL, rs1, gb);
+            const uint32_t s_lo = __shfl_sync(FULL, (uint32_t)Sc, gb), s_hi = __shfl_sync(FULL, (uint32_t)(Sc >> 32), gb);
+            const unsigned q = g.lane < u ? (unsigned)t2m.pos[g.lane * 32 + s] : 0u;
+            const uint32_t *rq = rows + (q >> 5);
+            const unsigned qb = q & 31u;
+            uint32_t row = 0u;
+#pragma unroll 4
+            for (unsigned j = 0; j < u; ++j) {
+                const unsigned qj = (unsigned)__shfl_sync(FULL, q, (int)j);
+                uint32_t w = 0u;
+                if (g.lane < u) w = SMEM ? rq[(size_t)qj * WP] : __ldg(rq + (size_t)qj * WP);
+                const unsigned b = __ballot_sync(FULL, (w >> qb) & 1u);
+                if (g.lane == j) row = b;
+            }
+            if (g.lane < u) t2m.A[g.lane * 32 + s] = row;
+            if (g.lane == s) {
+                t2.P = P0;
+                t2.X = X0;
+                t2.L = L0;
+                t2.rs = r0;
+                t2.S = (uint64_t)s_lo | ((uint64_t)s_hi << 32);
+                t2.d = 0;
+                t2.busy = true;
+            }
+        }
+        __syncwarp();
+        if (g.lane == 0) {
+            cn.note(kDiagLaneTasks, (unsigned long long)__popc(okl));
+            atomicAdd(&lq.h->t2_busy, (unsigned)__popc(okl));
+        }
+        return ok;
+    };
+
+    for (unsigned it = 0;;) {
+        // ---- T: the lane tier.  While this warp's lanes hold subproblems,
+        // a lane step advances every one of them by a node.  It runs when
+        // fewer lanes are free than the warp has groups (room is made before
+        // the groups may hand over more), and when no group of the warp has a
+        // frame -- then every 4th iteration still goes through A and B so
+        // idle groups can take frames.
+        bool t2any = false;
+        if (T2) {
+            const unsigned busym = __ballot_sync(FULL, t2.busy);
+            t2any = busym != 0u;
+            if (t2any) {
+                const unsigned g1 = __ballot_sync(FULL, work);
+                if (32u - (unsigned)__popc(busym) < GPW || (g1 == 0u && (++t2it & 3u) != 0u)) {
+                    t2_step<PIVOT>(t2, t2m, g.lane, hv, hk, hist, prm.out, prm.pivot_mode, t2_spill, cn,
+                                   &lq.h->t2_busy);
+                    continue;
+                }
+            }
+        }
+        ++it;  // group-search iterations: the periodic ring checks below count these
         // ---- A: a frame whose branching set is exhausted returns to its
         // parent (a stacked level always has children left), or the group's
         // work is done
@@ -1107,7 +1365,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             work = false;
             lempty = false;
             if (g.leader()) {
-                cn.busy += global_ns() - t_busy;
+                cn.note(kDiagBusyNs, global_ns() - t_busy);
                 atomicAdd(&lq.h->idle, 1u);
                 // the last work of the block gives back its unit
                 if (atomicSub(&lq.h->bwork, 1u) == 1u) atomicSub(&ctl->pending, 1u);
@@ -1128,7 +1386,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             lt = __shfl_sync(FULL, lt, 0);
             li = __shfl_sync(FULL, li, 0);
             ld = __shfl_sync(FULL, ld, 0);
-            if (busy_b == 0u && ld) break;
+            if (busy_b == 0u && ld && !t2any) break;
             const unsigned lqueued = lt - lh;
             unsigned ticket = 0, got = 0;
             if (!work && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, ticket) ? 1u : 0u;
@@ -1157,7 +1415,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     __threadfence_block();
                     vst(&lq.seq[ticket & (kLocalSlots - 1)], ticket + kLocalSlots);
                     atomicSub(&lq.h->idle, 1u);
-                    ++cn.steals;
+                    cn.note(kDiagSteals);
                 }
                 start_frame();
             }
@@ -1169,19 +1427,29 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         }
 
         // ---- B2: the global ring and the end of the search.  Global state is
-        // read by the block's polling warp (an all-idle warp) or, at most
-        // every tune.refresh_ns, by one busy warp, and cached in shared memory.
+        // read by the block's polling warp or, at most every tune.refresh_ns,
+        // by one busy warp, and cached in shared memory.  The polling role
+        // goes to a warp with an idle group (while the role is vacant) and
+        // stays with it until its groups are all busy; the poller comes here
+        // every iteration and asks the global ring for frames for its idle
+        // groups when the block's ring is empty.
         const unsigned busy2 = __ballot_sync(FULL, work);
-        if (busy2 == 0u || (it & (prm.tune.global_check - 1u)) == 0u) {
+        const unsigned idle_leads = __ballot_sync(FULL, !work && g.leader());
+        bool vacant = false;
+        if (idle_leads != 0u && !poller) vacant = __shfl_sync(FULL, g.lane == 0 ? vld(&lq.h->poller) : 1u, 0) == 0u;
+        if (busy2 == 0u || poller || vacant || (it & (prm.tune.global_check - 1u)) == 0u) {
             unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
             bool pol = poller;
             if (g.lane == 0) {
                 lh = vld(&lq.h->head);
                 lt = vld(&lq.h->tail);
-                if (busy2 == 0u && !pol) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
+                if (idle_leads != 0u && !pol) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
                 const uint64_t now = global_ns();
-                bool refresh = pol;
-                if (!refresh && now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) > prm.tune.refresh_ns)
+                // a poller with busy groups refreshes at most every quarter of
+                // refresh_ns (its own frames come first); an all-idle one always
+                const uint64_t age = now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp);
+                bool refresh = pol && (busy2 == 0u || age > prm.tune.refresh_ns / 4u);
+                if (!refresh && !pol && age > prm.tune.refresh_ns)
                     refresh = atomicCAS(&lq.h->refreshing, 0u, 1u) == 0u;
                 if (refresh) {
                     ab = ld_relaxed(&ctl->abort);
@@ -1212,7 +1480,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                             const unsigned qg = min(tail - head, 65535u), sv = min(starving, 65535u);
                             unsigned long long *rec = prm.trace + 2ull * ((size_t)blockIdx.x * prm.trace_per_block + ti);
                             rec[0] = now;
-                            rec[1] = (unsigned long long)busy | ((unsigned long long)min(lt - lh, 65535u) << 16) |
+                            rec[1] = (unsigned long long)busy | ((unsigned long long)min(vld(&lq.h->t2_busy), 65535u) << 16) |
                                      ((unsigned long long)qg << 32) | ((unsigned long long)sv << 48);
                         }
                     }
@@ -1237,7 +1505,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             lt = __shfl_sync(FULL, lt, 0);
             done = __shfl_sync(FULL, done, 0);
             if (ab) break;
-            if (busy2 == 0u && done) break;
+            if (busy2 == 0u && done && !t2any) break;
             const unsigned queued = tail - head;
             gq = queued;
 
@@ -1256,16 +1524,16 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             const unsigned askers = __ballot_sync(FULL, ask);
             if (!ring_shared) {
                 if (ask) {
-                    ++cn.gtry;
-                    got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.cas_fail, prm.tune.pop_tries) ? 1u : 0u;
+                    cn.note(kDiagGtry);
+                    got = q_reserve_pop(ctl, prm.seq, qmask, ticket, cn.diag + kDiagCasFail, prm.tune.pop_tries) ? 1u : 0u;
                 }
             } else if (askers != 0u) {
                 const unsigned lead = (unsigned)(__ffs(askers) - 1);
                 unsigned first = 0u, k = 0u;
                 if (g.lane == lead) {
-                    ++cn.gtry;
+                    cn.note(kDiagGtry);
                     k = q_reserve_pop_many(ctl, prm.seq, qmask, min(4u, (unsigned)__popc(askers)), first,
-                                           cn.cas_fail, prm.tune.pop_tries);
+                                           cn.diag + kDiagCasFail, prm.tune.pop_tries);
                 }
                 k = __shfl_sync(FULL, k, (int)lead);
                 first = __shfl_sync(FULL, first, (int)lead);
@@ -1301,13 +1569,14 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     atomicSub(&lq.h->idle, 1u);
                     // an already active block absorbs the frame's unit
                     if (atomicAdd(&lq.h->bwork, 1u) != 0u) atomicSub(&ctl->pending, 1u);
-                    ++cn.steals;
-                    ++cn.gsteals;
+                    cn.note(kDiagSteals);
+                    cn.note(kDiagGlobal);
                 }
                 start_frame();
             }
-            if (poller && __ballot_sync(FULL, work) != 0u) {
-                // busy now: hand the polling role to another idle warp
+            if (poller && __ballot_sync(FULL, !work && g.leader()) == 0u) {
+                // every group busy now: hand the polling role to a warp with
+                // an idle group
                 if (g.lane == 0) atomicExch(&lq.h->poller, 0u);
                 poller = false;
             }
@@ -1321,6 +1590,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (__ballot_sync(FULL, hungry) != 0u) share(hungry, false, gmin);
 
             if (__ballot_sync(FULL, work) == 0u) {
+                if (T2 && t2any) continue;  // no frame, but subproblems: back to the lane tier
                 // nobody here has work: back off; the poller watches for a
                 // stalled search
                 if (g.lane == 0 && poller) {
@@ -1468,6 +1738,18 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         bool hasLc, more;
         g.any2(Lc, L, hasLc, more);
         bool desc = inter && hasLc;
+        if (T2 && t2p != 0u) {
+            // a child whose P' u X' has at most 32 vertices and whose P' is
+            // small enough goes to a free lane of the warp instead
+            int cu = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) cu += (__popc(Pc[k] | Xc[k]) << 16) | __popc(Pc[k]);
+            cu = g.sum(cu);
+            const bool comp = desc && (cu >> 16) <= 32 && (unsigned)(cu & 0xffff) <= t2p;
+            if (__ballot_sync(FULL, comp) != 0u) {
+                if (t2_take(comp, Pc, Xc, Lc, rs + 1u, Sc)) desc = false;
+            }
+        }
         // Breadth-first split of the top of the tree: a new subtree with a
         // large candidate set goes to the global ring (while the ring is short
         // of frames; gq is the same in every lane) instead of being descended
@@ -1489,7 +1771,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             const bool pushed = push_global<G, K>(g, prm, sp, Pc, Xc, (unsigned)pc | (n << 16), rs + 1u, Sc, list, sR, cn);
             if (pushed) {
                 desc = false;
-                if (g.leader()) ++cn.don;
+                if (g.leader()) cn.note(kDiagDonations);
             }
         }
         bool spill = false;
@@ -1509,7 +1791,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             for (int k = 0; k < K; ++k) sR[k] = 0u;
             if (list && spill) r_bits(rs, -1, sR);
             const bool pushed = push_global<G, K>(g, prm, spill, P, X, pe, rs, S, list, sR, cn);
-            if (pushed && g.leader()) ++cn.don;
+            if (pushed && g.leader()) cn.note(kDiagDonations);
             if (spill && !pushed && g.leader()) set_status(prm.out, ctl, MCE_EOVERFLOW);
         }
         lempty = (act && !desc && !more) || (work && v < 0);
@@ -1564,11 +1846,13 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
                                              prm.tune.share_global, prm.split_min_p, &deg_sum);
     uint32_t *stack_smem = reinterpret_cast<uint32_t *>(smem_raw + prm.stack_offset);
     Counters cn;
+    cn.diag = lq.h->diag;
     if (ok)
         search_loop<G, K, SMEM, PIVOT, LIST>(prm, SMEM ? srows : prm.rows, hv, hk, hist, lq, th, stack_smem,
-                                       (int)prm.stack_smem_levels, cn);
+                                       (int)prm.stack_smem_levels, smem_raw + prm.t2_offset, cn);
     flush_counters(cn, prm.out);
     __syncthreads();
+    if (threadIdx.x == 0) flush_diag(lq.h->diag, prm.out);
     for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x)
         if (hist[i]) atomicAdd(reinterpret_cast<unsigned long long *>(prm.out + MCE_OUT_HIST + i), (unsigned long long)hist[i]);
 }
@@ -1738,15 +2022,24 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         prm.trace_per_block = 0;
         prm.tune = bp.tune;
         prm.lst = ListParams{};
+        prm.part = nullptr;
+        prm.part_k = 0;
+        prm.count_root = 1;
+        prm.seed_children = 0;
+        prm.t2_offset = bp.t2_offset;
+        prm.t2_levels = bp.t2_levels;
+        prm.t2_max_p = bp.t2_max_p;
         const Thresholds th = density_thresholds(SMEM ? srows : gd.ren, n, WP, bp.tune.share_local,
                                                  bp.tune.share_global, bp.split_min_p, &root_key);
         Counters cn;
+        cn.diag = lq.h->diag;
         if (ok)
             search_loop<G, K, SMEM, PIVOT, false>(prm, SMEM ? srows : gd.ren, hv, hk, hist, lq, th,
                                            reinterpret_cast<uint32_t *>(smem_raw + bp.stack_offset),
-                                           (int)bp.stack_smem_levels, cn);
+                                           (int)bp.stack_smem_levels, smem_raw + bp.t2_offset, cn);
         flush_counters(cn, gd.out);
         __syncthreads();
+        if (threadIdx.x == 0) flush_diag(lq.h->diag, gd.out);
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x)
             if (hist[j]) atomicAdd(reinterpret_cast<unsigned long long *>(gd.out + MCE_OUT_HIST + j), (unsigned long long)hist[j]);
         __syncthreads();
@@ -1771,7 +2064,10 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
     // the part-frames kernel that follows) and counts the root only when
     // asked to
     const bool part = prm.part != nullptr;
-    const unsigned queued = part ? prm.part_k : (n > 0u ? 1u : 0u);
+    // seeded: the root's children are queued by the seeding kernel that
+    // follows, so the queue starts empty here
+    const bool seeded = part || prm.seed_children;
+    const unsigned queued = part ? prm.part_k : (prm.seed_children ? 0u : (n > 0u ? 1u : 0u));
     const bool root = !part || prm.count_root;
     for (unsigned i = tid; i < prm.qcap; i += nth) prm.seq[i] = i < queued ? i + 1u : i;
     for (unsigned i = tid; i < MCE_OUT_WORDS(n); i += nth) {
@@ -1784,7 +2080,7 @@ __global__ void search_init_kernel(const SearchParams prm, const unsigned *root_
         if (i == MCE_OUT_GROUPS) v = prm.total_groups;
         prm.out[i] = v;
     }
-    if (part) {
+    if (seeded) {
         if (tid == 0) {
             Ctl *c = prm.ctl;
             c->head = 0u;

@@ -22,6 +22,9 @@ cudaError_t run_search_t(const SearchParams &prm, const LaunchShape &sh, cudaStr
     if (prm.part) {
         e = launch_part_frames(prm, rp, s);
         if (e != cudaSuccess) return e;
+    } else if (prm.seed_children) {
+        e = launch_seed_children(prm, rp, s);
+        if (e != cudaSuccess) return e;
     }
     e = kernel_smem_setup((const void *)search_kernel<G, K, SMEM, PIVOT, LIST>);
     if (e != cudaSuccess) return e;

@@ -116,6 +116,46 @@ __global__ void part_frames_kernel(const SearchParams prm, const unsigned *root_
     }
 }
 
+// Every root child as its own frame, one block per candidate child t < n.
+__global__ void seed_children_kernel(const SearchParams prm, const unsigned *root_pivot)
+{
+    __shared__ int v;
+    __shared__ uint32_t c;
+    const uint32_t t = blockIdx.x;
+    const uint32_t n = prm.n, wp = prm.wp;
+    const uint32_t p0 = root_pivot ? *root_pivot : 0u;
+    const uint32_t *rp = prm.rows + (size_t)p0 * wp;
+    if (threadIdx.x == 0) {
+        uint32_t cnt = 0;
+        for (uint32_t w = 0; w * 32u < n; ++w) cnt += (uint32_t)__popc(valid_bits(w, n) & ~rp[w]);
+        c = cnt;
+        v = t < cnt ? select_child(prm.rows, n, wp, p0, t) : -1;
+    }
+    __syncthreads();
+    const bool go = prm.out[MCE_OUT_STATUS] == 0ull;  // an invalid input queues nothing
+    if (t == 0 && threadIdx.x == 0 && go) {
+        prm.ctl->tail = c;
+        prm.ctl->pending = c;
+    }
+    if (v < 0 || !go) return;
+    uint32_t *fr = prm.frames + (size_t)t * prm.fs;
+    for (uint32_t w = threadIdx.x; w < wp; w += blockDim.x) {
+        const uint32_t valid = valid_bits(w, n);
+        const uint32_t X = valid & ~rp[w] & below_bits(w, (uint32_t)v);
+        fr[kFrameHdr + w] = valid & ~X;
+        fr[kFrameHdr + wp + w] = X;
+        if (prm.lst.rec) fr[kFrameHdr + 2 * wp + w] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        fr[0] = (p0 & 0xffffu) | (((uint32_t)v + 1u) << 16);
+        fr[1] = 0u;
+        fr[2] = 0u;
+        fr[3] = 0u;
+        fr[4] = 0u;
+        prm.seq[t] = t + 1u;  // the frame is ready for consumer ticket t
+    }
+}
+
 // TomitaBB's root pivot: with X empty, the vertex of P = V with the most
 // neighbours in P (its degree), earliest in the order on ties.
 __global__ void root_degree_pivot_kernel(const uint32_t *rows, uint32_t n, uint32_t wp, unsigned *dst)
@@ -149,6 +189,13 @@ cudaError_t launch_root_children(const uint32_t *rows, uint32_t n, uint32_t wp, 
     const unsigned threads = 128;
     const unsigned blocks = (std::max<uint32_t>(n, 1u) + threads - 1) / threads;
     root_children_kernel<<<blocks, threads, 0, s>>>(rows, n, wp, root_pivot, sizes, cap, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_children(const SearchParams &prm, const unsigned *root_pivot, cudaStream_t s)
+{
+    if (prm.n == 0) return cudaSuccess;
+    seed_children_kernel<<<prm.n, 64, 0, s>>>(prm, root_pivot);
     return cudaGetLastError();
 }
 
