@@ -246,7 +246,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 0u, 1u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -1195,6 +1195,7 @@ struct Bucket {
     LaunchShape shape{};
     uint32_t qcap = 0, fs = 0, groups = 0;
     uint32_t stack_levels = 0, stack_offset = 0;
+    uint32_t t2_offset = 0, t2_levels = 0, t2_max_p = 0;  // lane tier (t2_max_p 0: off)
     size_t qstride = 0, list_off = 0, region_off = 0, next_off = 0;
 };
 
@@ -1445,7 +1446,19 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         for (uint32_t i : bk.graphs) base = std::max(base, search_smem(b->n[i], (uint32_t)(bk.G * bk.K), bk.smem));
         const unsigned threads = bk.threads;
         if (threads % 32 || threads > kMaxThreads) { rc = MCE_EINVAL; break; }
-        // at most 56 KB of stack per block, so that several blocks share an SM
+        // the lane tier's region (groups of two or more lanes) when it fits,
+        // then at most 56 KB of stack per block, so that several blocks share
+        // an SM
+        const Tuning tu = default_tuning();
+        if (bk.G >= 2 && tu.t2_p != 0u) {
+            const size_t off = round_up(base, 16), t2b = (size_t)(threads / 32) * t2_warp_bytes(tu.t2_levels);
+            if (off + t2b <= slimit) {
+                bk.t2_offset = (uint32_t)off;
+                bk.t2_levels = tu.t2_levels;
+                bk.t2_max_p = tu.t2_p;
+                base = off + t2b;
+            }
+        }
         size_t smem = 0;
         plan_stack_for((uint32_t)base, bk.G, bk.K, threads, std::min<size_t>(slimit, base + 56 * 1024),
                        bk.stack_levels, bk.stack_offset, smem);
@@ -1554,6 +1567,9 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
             bp.stack_smem_levels = bk.stack_levels;
             bp.stack_offset = bk.stack_offset;
             bp.tune = default_tuning();
+            bp.t2_offset = bk.t2_offset;
+            bp.t2_levels = bk.t2_levels;
+            bp.t2_max_p = bk.t2_max_p;
             ce = cudaStreamWaitEvent(b->side[i], b->events[0], 0);
             if (ce == cudaSuccess) ce = bk.impl.run_batch(bp, bk.shape, b->side[i]);
             if (ce == cudaSuccess) ce = cudaEventRecord(b->events[i + 1], b->side[i]);

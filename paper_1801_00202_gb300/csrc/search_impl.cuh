@@ -1427,29 +1427,21 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         }
 
         // ---- B2: the global ring and the end of the search.  Global state is
-        // read by the block's polling warp or, at most every tune.refresh_ns,
-        // by one busy warp, and cached in shared memory.  The polling role
-        // goes to a warp with an idle group (while the role is vacant) and
-        // stays with it until its groups are all busy; the poller comes here
-        // every iteration and asks the global ring for frames for its idle
-        // groups when the block's ring is empty.
+        // read by the block's polling warp (an all-idle warp) or, at most
+        // every tune.refresh_ns, by one busy warp, and cached in shared memory.
         const unsigned busy2 = __ballot_sync(FULL, work);
-        const unsigned idle_leads = __ballot_sync(FULL, !work && g.leader());
-        bool vacant = false;
-        if (idle_leads != 0u && !poller) vacant = __shfl_sync(FULL, g.lane == 0 ? vld(&lq.h->poller) : 1u, 0) == 0u;
-        if (busy2 == 0u || poller || vacant || (it & (prm.tune.global_check - 1u)) == 0u) {
+        if (busy2 == 0u || (it & (prm.tune.global_check - 1u)) == 0u) {
             unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
             bool pol = poller;
             if (g.lane == 0) {
                 lh = vld(&lq.h->head);
                 lt = vld(&lq.h->tail);
-                if (idle_leads != 0u && !pol) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
+                // the polling warp is one with nothing at all to do (no frame and no
+                // lane-tier subproblem): it polls every iteration
+                if (busy2 == 0u && !pol && !t2any) pol = atomicCAS(&lq.h->poller, 0u, 1u) == 0u;
                 const uint64_t now = global_ns();
-                // a poller with busy groups refreshes at most every quarter of
-                // refresh_ns (its own frames come first); an all-idle one always
-                const uint64_t age = now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp);
-                bool refresh = pol && (busy2 == 0u || age > prm.tune.refresh_ns / 4u);
-                if (!refresh && !pol && age > prm.tune.refresh_ns)
+                bool refresh = pol;
+                if (!refresh && now - *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) > prm.tune.refresh_ns)
                     refresh = atomicCAS(&lq.h->refreshing, 0u, 1u) == 0u;
                 if (refresh) {
                     ab = ld_relaxed(&ctl->abort);
@@ -1574,9 +1566,8 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 }
                 start_frame();
             }
-            if (poller && __ballot_sync(FULL, !work && g.leader()) == 0u) {
-                // every group busy now: hand the polling role to a warp with
-                // an idle group
+            if (poller && __ballot_sync(FULL, work) != 0u) {
+                // busy now: hand the polling role to another idle warp
                 if (g.lane == 0) atomicExch(&lq.h->poller, 0u);
                 poller = false;
             }
