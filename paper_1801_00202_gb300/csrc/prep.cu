@@ -123,12 +123,65 @@ __device__ __forceinline__ void order_body(uint32_t n, uint32_t w, const uint32_
     }
 }
 
-template <int JW>
+// The same order for one graph with the whole block (eight warps): thread t
+// owns the keys of vertices t, t + 256, ... (KP of them).  A round takes each
+// warp's maximum key (__reduce_max_sync), the block maximum through a
+// double-buffered slot per warp in shared memory (one barrier per round: a
+// warp cannot reach round i + 2's write before every warp has passed round
+// i + 1's barrier, after its reads of round i), places that vertex and
+// decrements the keys of its remaining neighbours.
+template <int KP>
 __global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
                                                    uint32_t *__restrict__ order, int rows_in_smem)
 {
     extern __shared__ __align__(16) uint32_t sm[];
-    order_body<JW>(n, w, rows, order, rows_in_smem, sm);
+    uint32_t *mx = sm;              // [2][8] warp maxima
+    uint32_t *srows = sm + 16;      // n * w words (optional)
+    const uint32_t *R = rows;
+    if (rows_in_smem) {
+        for (uint32_t i = threadIdx.x; i < n * w; i += blockDim.x) srows[i] = rows[i];
+        R = srows;
+    }
+    __syncthreads();
+    const uint32_t t = threadIdx.x;
+    uint32_t key[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        const uint32_t u = t + 256u * q;
+        uint32_t k = 0u;
+        if (u < n) {
+            uint32_t deg = 0;
+            for (uint32_t j = 0; j < w; ++j) deg += __popc(R[(size_t)u * w + j]);
+            k = ((deg + 1u) << 12) | (4095u - u);
+        }
+        key[q] = k;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t b = 0u;
+#pragma unroll
+        for (int q = 0; q < KP; ++q) b = key[q] > b ? key[q] : b;
+        b = __reduce_max_sync(FULLM, b);
+        volatile uint32_t *slot = mx + (i & 1u) * 8u;
+        if ((t & 31u) == 0u) slot[t >> 5] = b;
+        __syncthreads();
+        uint32_t best = slot[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) best = slot[j] > best ? slot[j] : best;
+        const uint32_t v = 4095u - (best & 4095u);
+        if (t == 0) order[i] = v;
+        const uint32_t *rv = R + (size_t)v * w;
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            const uint32_t u = t + 256u * q;
+            if (u < n) {
+                const uint32_t word = rv[u >> 5];
+                uint32_t k = key[q];
+                if (u == v) k = 0u;
+                else if (((word >> (u & 31u)) & 1u) && k) k -= 1u << 12;
+                key[q] = k;
+            }
+        }
+    }
 }
 
 // One block per graph of a batch; the rows go to shared memory when they fit
@@ -218,25 +271,20 @@ cudaError_t launch_validate_rows(uint32_t n, uint32_t w, const uint32_t *rows, u
 cudaError_t launch_order(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t *order, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    const size_t keys = ((n + 3u) & ~3u) * sizeof(uint32_t);
     const size_t rbytes = (size_t)n * w * 4;
-    const int in_smem = (keys + rbytes) <= 200u * 1024u;
-    const size_t smem = keys + (in_smem ? rbytes : 0);
-    const uint32_t words = (n + 31) / 32;  // words that can hold set bits
-    cudaError_t e;
-    if (words <= 32) {
-        e = kernel_smem_setup((const void *)order_kernel<1>);
-        if (e != cudaSuccess) return e;
-        order_kernel<1><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
-    } else if (words <= 64) {
-        e = kernel_smem_setup((const void *)order_kernel<2>);
-        if (e != cudaSuccess) return e;
-        order_kernel<2><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
-    } else {
-        e = kernel_smem_setup((const void *)order_kernel<4>);
-        if (e != cudaSuccess) return e;
-        order_kernel<4><<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
-    }
+    const int in_smem = (64 + rbytes) <= 200u * 1024u;
+    const size_t smem = 64 + (in_smem ? rbytes : 0);
+    const void *k = nullptr;
+    void (*f)(uint32_t, uint32_t, const uint32_t *, uint32_t *, int) = nullptr;
+    if (n <= 256) f = order_kernel<1>;
+    else if (n <= 512) f = order_kernel<2>;
+    else if (n <= 1024) f = order_kernel<4>;
+    else if (n <= 2048) f = order_kernel<8>;
+    else f = order_kernel<16>;
+    k = (const void *)f;
+    cudaError_t e = kernel_smem_setup(k);
+    if (e != cudaSuccess) return e;
+    f<<<1, 256, smem, s>>>(n, w, rows, order, in_smem);
     return cudaGetLastError();
 }
 
