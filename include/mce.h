@@ -318,6 +318,25 @@ void mce_graph_free(mce_graph *g);
  * buffers do not fit in device memory. */
 int mce_enumerate(mce_graph *g, const mce_options *opts, mce_result *res);
 
+/* Streaming listing: every maximal clique handed to the caller's sink in
+ * chunks, with no buffer sized up front (the listing output of the problem,
+ * Section 2).  The call first counts (an ordinary search; the histogram gives
+ * the exact number of cliques and member ids), then runs the listing search
+ * with device records of exactly that size, builds the listing on the device
+ * (each clique's labels ascending; with MCE_LIST_SORTED in opts->flags the
+ * cliques in lexicographic order, else in no particular order), and calls
+ * sink(ids, off, count, user) for consecutive chunks of up to 2^20 cliques:
+ * clique i of the chunk is ids[off[i] .. off[i+1]) (original labels, uint32),
+ * off has count + 1 entries and starts at 0.  The arrays live in pinned host
+ * memory of the context and are valid only during the call; a non-zero return
+ * from the sink stops the stream (the call still returns MCE_OK).  res gets
+ * the counters (and hist, if res->hist is set) as from mce_enumerate;
+ * res->list_* fields are left as the caller set them.  n = 0 gives one chunk
+ * with the empty clique.  Graphs held as adjacency lists: MCE_ENOTIMPL. */
+typedef int (*mce_clique_sink)(const uint32_t *ids, const uint64_t *off, uint64_t count, void *user);
+int mce_enumerate_stream(mce_graph *g, const mce_options *opts, mce_clique_sink sink, void *user,
+                         mce_result *res);
+
 /* The root's children as independent subtrees (the split of one search
  * over several GPUs).  Alg. 3 (Section 3.3) splits the enumeration into
  * independent subproblems because each branch of the sequential loop gets

@@ -126,7 +126,11 @@ _SIGS = {
     "mce_measure_peaks": (C.c_int, [C.c_int, C.POINTER(Peaks)]),
     "mce_root_children": (C.c_int, [_VP, C.POINTER(Options), _VP, _U32, C.POINTER(_U32)]),
     "mce_enumerate_part": (C.c_int, [_VP, C.POINTER(Options), _VP, _U32, C.c_int, C.POINTER(Result)]),
+    "mce_enumerate_stream": (C.c_int, [_VP, C.POINTER(Options), _VP, _VP, C.POINTER(Result)]),
 }
+
+# mce_clique_sink: int (*)(const uint32_t *ids, const uint64_t *off, uint64_t count, void *user)
+CliqueSink = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64), C.c_uint64, C.c_void_p)
 
 
 def lib():
@@ -417,6 +421,28 @@ class Graph:
                                       1 if count_root else 0, C.byref(r))
         if raise_on_error:
             _check(rc, "mce_enumerate_part")
+        return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
+                "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
+                "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}
+
+
+    def enumerate_stream(self, sink, opts: Options | None = None, raise_on_error: bool = True) -> dict:
+        """mce_enumerate_stream: every maximal clique handed to sink(ids,
+        off, count) in chunks (numpy copies: clique i is ids[off[i]:off[i+1]],
+        original labels); a truthy return from sink stops the stream."""
+        def _cb(ids_p, off_p, count, _user):
+            off = np.ctypeslib.as_array(off_p, shape=(count + 1,)).copy()
+            nid = int(off[-1])
+            ids = np.ctypeslib.as_array(ids_p, shape=(nid,)).copy() if nid else np.zeros(0, dtype=np.uint32)
+            return 1 if sink(ids, off, int(count)) else 0
+        cb = CliqueSink(_cb)
+        hist = np.zeros(self.n + 1, dtype=np.uint64)
+        r = Result()
+        r.hist = hist.ctypes.data_as(C.POINTER(C.c_uint64))
+        r.hist_cap = hist.size
+        rc = lib().mce_enumerate_stream(self.handle, _opt(opts), C.cast(cb, C.c_void_p), None, C.byref(r))
+        if raise_on_error:
+            _check(rc, "mce_enumerate_stream")
         return {"rc": rc, "count": r.count, "nodes": r.nodes, "internal": r.internal_nodes,
                 "dead_ends": r.dead_ends, "hash": r.hash, "max_size": r.max_size, "hist": hist,
                 "kernel_ms": r.kernel_ms, "total_ms": r.total_ms}

@@ -161,13 +161,13 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     c.threads = o.threads_per_block ? o.threads_per_block : kMaxThreads;
     if (c.threads % 32 || c.threads > kMaxThreads) return MCE_EINVAL;
 
-    // The lane tier (counting kernels, groups of two or more lanes; not in
-    // the served form, whose blocks stay small so that requests share SMs)
-    // needs t2_warp_bytes per warp.  Rows stay in shared memory when they fit
-    // beside it; otherwise they are read from L2, or, with t2_smem_rows, the
-    // block gets fewer warps so that they fit.
+    // The lane tier (counting kernels, groups of two or more lanes; in the
+    // served form, whose stack is capped so that requests share SMs, when
+    // serve_t2 is set) needs t2_warp_bytes per warp.  Rows stay in shared
+    // memory when they fit beside it; otherwise, with t2_smem_rows, the block
+    // gets fewer warps so that they fit, or they are read from L2.
     const Tuning tu = default_tuning();
-    const bool t2 = !c.list && G >= 2 && tu.t2_p != 0 && stack_cap == ~(size_t)0;
+    const bool t2 = !c.list && G >= 2 && tu.t2_p != 0 && (stack_cap == ~(size_t)0 || tu.serve_t2);
     const size_t t2w = t2 ? t2_warp_bytes(tu.t2_levels) : 0;
     auto fits = [&](bool rows_smem, unsigned threads) {
         return round_up(search_smem(n, c.wp, rows_smem, c.list), 16) + (size_t)(threads / 32) * t2w <= limit;
@@ -246,7 +246,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -267,6 +267,7 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "t2_levels")) d.t2_levels = std::min(val, 31u);
                 else if (!std::strcmp(key, "t2_smem_rows")) d.t2_smem_rows = val;
                 else if (!std::strcmp(key, "seed")) d.seed = val;
+                else if (!std::strcmp(key, "serve_t2")) d.serve_t2 = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -788,8 +789,10 @@ int fill_result(const std::vector<uint64_t> &h, uint32_t n, mce_result *res)
 namespace {
 // children / k / count_root: a part of the root's branching (children null:
 // the whole search).
+struct Sink;
 int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0,
-                   const uint32_t *children = nullptr, uint32_t k = 0, uint32_t count_root = 1);
+                   const uint32_t *children = nullptr, uint32_t k = 0, uint32_t count_root = 1,
+                   const Sink *sink = nullptr);
 }
 
 namespace {
@@ -1026,8 +1029,49 @@ cudaError_t copy_to_host(mce_ctx *ctx, void *dst, const void *src, size_t bytes,
 
 // CSR listing from a finished listing search (result words h) into the
 // caller's host buffers.
+// A caller's sink of listed cliques (mce_enumerate_stream), or none.
+struct Sink {
+    mce_clique_sink fn = nullptr;
+    void *user = nullptr;
+};
+
+// The device CSR (ids, off; count cliques) to the sink in chunks that fit
+// the context's pinned staging halves: offsets of up to 2^20 cliques in one
+// half, their member ids in the other; the offsets handed over are rebased
+// to the chunk.  A non-zero return of the sink stops the stream.
+int stream_to_sink(mce_ctx *ctx, const uint32_t *d_ids, const uint64_t *d_off, uint64_t count, const Sink &sk,
+                   cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (!ctx->stage[i]) e = cudaHostAlloc(&ctx->stage[i], kStageBytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) return MCE_ENOMEM;
+    uint64_t *hoff = static_cast<uint64_t *>(ctx->stage[0]);
+    uint32_t *hids = static_cast<uint32_t *>(ctx->stage[1]);
+    const uint64_t max_cliques = std::min<uint64_t>(1u << 20, kStageBytes / 8 - 1);
+    for (uint64_t c0 = 0; c0 < count;) {
+        uint64_t k = std::min<uint64_t>(count - c0, max_cliques);
+        e = cudaMemcpyAsync(hoff, d_off + c0, (k + 1) * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return MCE_ECUDA;
+        const uint64_t base = hoff[0];
+        while (k > 1 && (hoff[k] - base) * 4 > kStageBytes) k = (k + 1) / 2;  // members must fit one half
+        const uint64_t nid = hoff[k] - base;
+        if (nid * 4 > kStageBytes) return MCE_ENOMEM;  // one clique larger than a staging half
+        e = cudaMemcpyAsync(hids, d_ids + base, nid * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return MCE_ECUDA;
+        for (uint64_t i = 0; i <= k; ++i) hoff[i] -= base;
+        if (sk.fn(hids, hoff, k, sk.user) != 0) break;
+        c0 += k;
+    }
+    return MCE_OK;
+}
+
 int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d_order,
-                 const std::vector<uint64_t> &h, bool sorted, mce_result *res, cudaStream_t s)
+                 const std::vector<uint64_t> &h, bool sorted, mce_result *res, cudaStream_t s,
+                 const Sink &sk = Sink{})
 {
     const uint64_t count = h[MCE_OUT_COUNT];
     uint64_t ids = 0;
@@ -1038,11 +1082,14 @@ int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl[1], la.prm.overflow, 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return MCE_ECUDA;
-    const bool fits = res->list_off && res->list_off_cap >= count + 1 && (ids == 0 || (res->list_ids && res->list_cap >= ids));
+    const bool fits = sk.fn || (res->list_off && res->list_off_cap >= count + 1 &&
+                                (ids == 0 || (res->list_ids && res->list_cap >= ids)));
     if (!fits) return MCE_ETRUNC;
     if (ctl[1]) return MCE_ENOMEM;  // the caller's buffers fit, the device records did not
     if (n == 0) {                   // the empty set, reported by the root
-        res->list_off[0] = res->list_off[1] = 0;
+        uint64_t off[2] = {0, 0};
+        if (sk.fn) sk.fn(nullptr, off, 1, sk.user);
+        else res->list_off[0] = res->list_off[1] = 0;
         return MCE_OK;
     }
     ListJob j{};
@@ -1068,6 +1115,11 @@ int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d
     j.temp = m + ib + ob;
     j.temp_bytes = tb;
     e = list_build(j, s);
+    if (sk.fn) {
+        rc = e == cudaSuccess ? stream_to_sink(ctx, j.ids_out, j.off_out, count, sk, s) : MCE_ECUDA;
+        dfree(ctx, mem, ib + ob + tb, s);
+        return rc;
+    }
     if (e == cudaSuccess) e = copy_to_host(ctx, res->list_ids, j.ids_out, ids * 4, s);
     if (e == cudaSuccess) e = copy_to_host(ctx, res->list_off, j.off_out, (count + 1) * 8, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1076,7 +1128,7 @@ int list_deliver(mce_ctx *ctx, uint32_t n, const ListArea &la, const uint32_t *d
 }
 
 int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chrono::steady_clock::time_point t0,
-                   const uint32_t *children, uint32_t k, uint32_t count_root)
+                   const uint32_t *children, uint32_t k, uint32_t count_root, const Sink *sink)
 {
     mce_ctx *ctx = g->ctx;
     const bool listing = (o.flags & kListFlags) != 0u;
@@ -1125,7 +1177,8 @@ int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chr
         res->kernel_ms = kms;
         if (listing && rc == MCE_OK) {
             const uint32_t *d_order = reinterpret_cast<const uint32_t *>(static_cast<unsigned char *>(scr) + L.order);
-            rc = list_deliver(ctx, g->n, la, d_order, h, (o.flags & MCE_LIST_SORTED) != 0u, res, ctx->stream);
+            rc = list_deliver(ctx, g->n, la, d_order, h, (o.flags & MCE_LIST_SORTED) != 0u, res, ctx->stream,
+                              sink ? *sink : Sink{});
         }
     }
     if (la.mem) dfree(ctx, la.mem, la.bytes, ctx->stream);
@@ -1139,6 +1192,52 @@ int enumerate_once(mce_graph *g, const mce_options &o, mce_result *res, std::chr
     return rc;
 }
 }  // namespace
+
+extern "C" int mce_enumerate_stream(mce_graph *g, const mce_options *opts, mce_clique_sink sink, void *user,
+                                    mce_result *res)
+{
+    if (!g || !sink || !res) return MCE_EINVAL;
+    if (!g->d_rows) return MCE_ENOTIMPL;
+    const auto t0 = std::chrono::steady_clock::now();
+    DevicePick pick(g->ctx->device);
+    mce_options o = defaults(opts);
+    if (o.flags & MCE_OUTER) return MCE_ENOTIMPL;
+    if (!(o.flags & kListFlags)) o.flags |= MCE_LIST;
+    // a counting search first: the listing search's device records are then
+    // sized exactly (count cliques, sum of sizes member ids)
+    mce_options oc = o;
+    oc.flags &= ~kListFlags;
+    std::vector<uint64_t> hist((size_t)g->n + 1, 0);
+    mce_result r0{};
+    r0.hist = hist.data();
+    r0.hist_cap = g->n + 1;
+    int rc = mce_enumerate(g, &oc, &r0);
+    if (rc != MCE_OK) return rc;
+    uint64_t ids = 0;
+    for (uint32_t k = 0; k <= g->n; ++k) ids += (uint64_t)k * hist[k];
+    mce_result rl = *res;
+    rl.list_ids = nullptr;
+    rl.list_cap = ids;
+    rl.list_off = nullptr;
+    rl.list_off_cap = r0.count + 1;
+    const Sink sk{sink, user};
+    rc = enumerate_once(g, o, &rl, t0, nullptr, 0, 1, &sk);
+    for (int tries = 0; rc == MCE_EOVERFLOW && tries < 2; ++tries) {
+        Config c;
+        if (choose(g->n, o, c) != MCE_OK) break;
+        uint32_t lg = 0;
+        while ((1u << lg) < c.qcap) ++lg;
+        if (lg + 4 > 24) break;
+        o.queue_log2 = lg + 4;
+        rc = enumerate_once(g, o, &rl, t0, nullptr, 0, 1, &sk);
+    }
+    rl.list_ids = res->list_ids;
+    rl.list_cap = res->list_cap;
+    rl.list_off = res->list_off;
+    rl.list_off_cap = res->list_off_cap;
+    *res = rl;
+    return rc;
+}
 
 // ---------------------------------------------------------------------------
 // Batched form

@@ -96,6 +96,7 @@ struct Tuning {
     uint32_t t2_levels;     // lane tier: explicit-stack levels per lane in shared memory
     uint32_t t2_smem_rows;  // lane tier on: keep the rows in shared memory (fewer warps) when 1
     uint32_t seed;          // start from every root child as its own queued frame (1) or the root (0)
+    uint32_t serve_t2;      // served requests use the lane tier too (its region beside the capped stack)
 };
 
 // The lane tier (second search tier): a frame whose P u X has at most 32

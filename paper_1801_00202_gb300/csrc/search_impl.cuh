@@ -95,7 +95,10 @@ __device__ __forceinline__ Thresholds density_thresholds(const uint32_t *rows, u
         // graph also counts as big.
         t.share_local = min((unsigned)kShareLocalByDensity[i - 1], max(16u, n / 8u));
         t.share_global = min((unsigned)kShareGlobalByDensity[i - 1], max(20u, n / 4u));
-        t.split = kSplitByDensity[i - 1];
+        // dense structured graphs (Moon-Moser: every child keeps all but three
+        // vertices) would never reach the density's split size; cap it at two
+        // thirds of n
+        t.split = min((unsigned)kSplitByDensity[i - 1], max(24u, 2u * n / 3u));
     }
     if (fixed_local) t.share_local = fixed_local;
     if (fixed_global) t.share_global = fixed_global;

@@ -207,3 +207,69 @@ def test_gnp_1000_listing_against_stored_oracle(ctx, mce):
         common = adj[K].all(axis=0)
         common[K] = False
         assert not common.any()
+
+
+# --- streaming listing (mce_enumerate_stream): no buffers sized up front ------
+
+def _mix64_np(z):
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= np.uint64(0xBF58476D1CE4E5B9)
+        z ^= z >> np.uint64(27)
+        z *= np.uint64(0x94D049BB133111EB)
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def _stream_summary(chunks, n):
+    """count, histogram and clique hash of streamed (ids, off) chunks,
+    vectorised: S(K) = sum of mix64(label + 1), h(K) = mix64(S ^ mix64(|K|))."""
+    count, hist, h = 0, np.zeros(n + 1, dtype=np.uint64), np.uint64(0)
+    for ids, off in chunks:
+        k = np.diff(off).astype(np.int64)
+        count += k.size
+        np.add.at(hist, k, 1)
+        terms = _mix64_np(ids.astype(np.uint64) + np.uint64(1))
+        with np.errstate(over="ignore"):
+            s = np.add.reduceat(terms, off[:-1].astype(np.int64)) if ids.size else np.zeros(k.size, np.uint64)
+            s[k == 0] = 0
+            h = h + np.sum(_mix64_np(s ^ _mix64_np(k.astype(np.uint64))), dtype=np.uint64)
+    return count, hist, int(h)
+
+
+@pytest.mark.parametrize("sort", [True, False])
+@pytest.mark.parametrize("n,p,seed", [(0, 0.0, 0), (1, 0.0, 0), (60, 0.5, 30), (300, 0.4, 31), (1100, 0.05, 32)])
+def test_streamed_listing_equals_oracle(ctx, mce, sort, n, p, seed):
+    uv = synth.gnp(n, p, seed) if n > 1 else synth.empty(n)
+    g = ctx.load_edges(n, uv)
+    got = []
+    try:
+        flags = mce.MCE_LIST_SORTED if sort else mce.MCE_LIST
+        res = g.enumerate_stream(lambda ids, off, k: got.extend(
+            tuple(int(x) for x in ids[off[i]:off[i + 1]]) for i in range(k)), mce.options(flags=flags))
+    finally:
+        g.free()
+    ref = oracle.tomita(n, uv, listing=True)
+    want = ref["listing"]
+    assert (res["count"], res["hash"]) == (ref["count"], ref["hash"])
+    assert (got if sort else sorted(got)) == want
+
+
+def test_streamed_listing_full_size_and_early_stop(ctx, mce):
+    gold = json.load(open(os.path.join(GOLDEN, "config_results.json")))["gnp_1000_0.3_s1"]
+    n, uv = 1000, synth.gnp(1000, 0.3, 1)
+    g = ctx.load_edges(n, uv)
+    chunks = []
+    try:
+        res = g.enumerate_stream(lambda ids, off, k: chunks.append((ids, off)))
+        count, hist, h = _stream_summary(chunks, n)
+        assert count == res["count"] == gold["count"]
+        assert h == gold["hash"] == res["hash"]
+        assert {str(k): int(v) for k, v in enumerate(hist) if v} == gold["hist"]
+        assert len(chunks) > 1                                   # 15.4 M cliques come in several chunks
+        seen = []
+        res2 = g.enumerate_stream(lambda ids, off, k: seen.append(k) or True)   # stop after the first chunk
+        assert res2["rc"] == 0 and len(seen) == 1
+    finally:
+        g.free()
