@@ -416,9 +416,11 @@ int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
  * others already on the GPU; mce_poll never blocks.  Each admitted request
  * runs its whole path on one of 128 streams with a grid sized by its expected
  * cost; requests overlap on the device only as far as CUDA maps their streams
- * to separate hardware queues, so set CUDA_DEVICE_MAX_CONNECTIONS=32 in the
- * environment before the process creates its CUDA context (the Python
- * binding does this when imported first). */
+ * to separate hardware queues (CUDA_DEVICE_MAX_CONNECTIONS, read when a
+ * context is created).  Loading the library sets it to 32 unless the process
+ * set it already, so a process that loads the library before it creates its
+ * CUDA context gets 32 queues; one that created its context first keeps the
+ * value it had then. */
 int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out);
 int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res);
 int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res);

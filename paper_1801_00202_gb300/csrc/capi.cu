@@ -22,6 +22,12 @@ using namespace mce;
 
 namespace {
 
+// The served form runs each admitted request on one of many streams, and CUDA
+// maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless
+// set), read when a context is created.  A process that loads the library
+// before it creates its CUDA context gets 32 unless it chose a value itself.
+__attribute__((constructor)) void default_connections() { setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0); }
+
 // ---------------------------------------------------------------------------
 // Launch configuration
 

@@ -105,10 +105,13 @@ struct Tuning {
 // A[row][lane] (u32), the positions of their local vertices pos[v][lane]
 // (u16), and t2_levels explicit-stack levels of six words per lane
 // [level][field][lane] (P, X, L, |R|, S low, S high).
+// After them, 512 bytes of scratch for the group search's parallel pivot
+// scoring (each lane's words of P').
 constexpr int kT2Fields = 6;
+constexpr int kPivotScratchWords = 128;
 __host__ __device__ inline size_t t2_warp_bytes(uint32_t levels)
 {
-    return 32 * 32 * 4 + 32 * 32 * 2 + (size_t)levels * kT2Fields * 32 * 4;
+    return 32 * 32 * 4 + 32 * 32 * 2 + (size_t)levels * kT2Fields * 32 * 4 + kPivotScratchWords * 4;
 }
 
 struct SearchParams {

@@ -898,6 +898,7 @@ struct T2Warp {
     uint32_t *A;    // [32 local rows][32 lanes]
     uint16_t *pos;  // [32 local vertices][32 lanes]: position in the order
     uint32_t *stk;  // [levels][kT2Fields][32 lanes]
+    uint32_t *piv;  // kPivotScratchWords: the lanes' words of P' (pivot scoring)
     int levels;
 };
 
@@ -1061,6 +1062,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         t2m.A = reinterpret_cast<uint32_t *>(wb);
         t2m.pos = reinterpret_cast<uint16_t *>(wb + 32 * 32 * 4);
         t2m.stk = reinterpret_cast<uint32_t *>(wb + 32 * 32 * 4 + 32 * 32 * 2);
+        t2m.piv = t2m.stk + (size_t)prm.t2_levels * kT2Fields * 32;
         t2m.levels = (int)prm.t2_levels;
     }
     unsigned t2it = 0;
@@ -1669,6 +1671,56 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         int pc;
         if (PIVOT == MCE_PIVOT_GREEDY) {
             pc = pg;
+        } else if (T2 && prm.t2_max_p != 0u) {
+            // argmax |P' n N(u)| over X' (TX, NX) or P' u X' (TomitaBB), all
+            // candidates at once: the lanes' words of P' go to the warp's
+            // scratch, every lane scores the candidates in its own words
+            // against the whole of P' (16-byte loads starting at a chunk
+            // rotated by lane, so a phase of eight lanes hits distinct
+            // banks), and one packed max (score + 1, 0xffff - position) over
+            // the group keeps the highest score, earliest on ties.  NX has
+            // TX's pivot (its early exit only saves work).
+            Stk::st_vec(t2m.piv + g.lane * K, Pc);
+            __syncwarp();
+            const uint32_t *pw = t2m.piv + g.gbase * K;  // this group's P' (WP words)
+            unsigned best = 0u;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                uint32_t w = 0u;
+                if (inter) w = (PIVOT == MCE_PIVOT_GREEDY_TX) ? (bx ? Xc[k] : 0u) : (Pc[k] | Xc[k]);
+                while (w) {
+                    const unsigned b = (unsigned)(__ffs(w) - 1);
+                    w &= w - 1u;
+                    const unsigned u = (g.gl * K + k) * 32u + b;
+                    const uint32_t *ru = rows + (size_t)u * WP;
+                    int c = 0;
+                    if (WP >= 4) {
+                        constexpr int NC = WP >= 4 ? WP / 4 : 1;
+#pragma unroll 4
+                        for (int j = 0; j < NC; ++j) {
+                            const int jj = ((j + (int)g.lane) & (NC - 1)) * 4;
+                            const uint4 a = *reinterpret_cast<const uint4 *>(pw + jj);
+                            const uint4 r = SMEM ? *reinterpret_cast<const uint4 *>(ru + jj)
+                                                 : __ldg(reinterpret_cast<const uint4 *>(ru + jj));
+                            c += __popc(a.x & r.x) + __popc(a.y & r.y) + __popc(a.z & r.z) + __popc(a.w & r.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < WP; ++j) c += __popc(pw[j] & (SMEM ? ru[j] : __ldg(ru + j)));
+                    }
+                    const unsigned key = ((unsigned)(c + 1) << 16) | (0xffffu - u);
+                    best = key > best ? key : best;
+                }
+            }
+            if (G > 1) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const unsigned y = __shfl_xor_sync(FULL, best, o);
+                    best = y > best ? y : best;
+                }
+            }
+            __syncwarp();
+            pc = best ? (int)(0xffffu - (best & 0xffffu)) : ((PIVOT == MCE_PIVOT_GREEDY_TX) ? fp : -1);
         } else {
             // argmax |P' n N(u)| over X' (TX) or P' u X' (TomitaBB); scanning
             // candidates in increasing position with '>' keeps the earliest

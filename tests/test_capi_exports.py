@@ -46,3 +46,20 @@ def test_host_only_calls(lib):
     assert m.mce_order(m.MCE_NMAX + 1, 200, 0, 0) == m.MCE_EINVAL
     assert m.mce_renumber(10, 0, 0, 0, 1, 0) == m.MCE_EINVAL
     assert m.mce_enumerate_device(10, 1, None, None, None, 0, None) == m.MCE_EINVAL
+
+
+def test_loading_the_library_asks_for_32_hardware_queues():
+    # a process that loads libmce before creating a CUDA context gets 32
+    # stream queues for the served form unless it set its own value
+    import subprocess
+    import sys
+    import paper_1801_00202_gb300 as m
+    m.build()
+    code = ("import ctypes; ctypes.CDLL(%r); libc = ctypes.CDLL(None); libc.getenv.restype = ctypes.c_char_p; "
+            "v = libc.getenv(b'CUDA_DEVICE_MAX_CONNECTIONS'); print(v.decode() if v else None)" % m._LIB_PATH)
+    env = {k: v for k, v in os.environ.items() if k != "CUDA_DEVICE_MAX_CONNECTIONS"}
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "32", r.stderr[-500:]
+    env["CUDA_DEVICE_MAX_CONNECTIONS"] = "4"
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert r.stdout.strip() == "4"
