@@ -623,6 +623,40 @@ def run_sweep(args):
     return 0
 
 
+def run_batch_probe(args):
+    """The first --batch-probe graphs of the batched workload as one batch
+    with the default launch choices: three warm-up launches, then one timed
+    launch (the case the ncu captures of batch_kernel profile)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32))) as pool:
+        specs = pool.map(_gen_batch, range(args.batch_probe), chunksize=16)
+    import torch
+
+    import paper_1801_00202_gb300 as mce
+    mce.build()
+    mce.lib()
+    ctx = mce.Context(0)
+    graphs = [ctx.load_bitset(n, rows) for n, _, _, rows in specs]
+    b = mce.Batch(ctx, graphs)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    b.launch()
+    res = b.results()
+    dt = time.perf_counter() - t
+    print(json.dumps({"batch_probe": len(graphs), "ms": 1e3 * dt, "graphs_per_s": len(graphs) / dt,
+                      "cliques": sum(r["count"] for r in res), "status_ok": all(r["status"] == 0 for r in res),
+                      "buckets": [{k: x[k] for k in ("words_class", "graphs", "lanes_per_subtree", "words_per_lane",
+                                                     "threads_per_block", "blocks")} for x in b.buckets()]}),
+          flush=True)
+    b.close()
+    for g in graphs:
+        g.free()
+    ctx.close()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -920,6 +954,8 @@ def main():
     ap.add_argument("--sweep-min-n", type=int, default=0)
     ap.add_argument("--batch-graphs", type=int, default=BATCH_GRAPHS)
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-probe", type=int, default=0,
+                    help="instead of the benchmark: time one launch of a batch of the first N batched graphs")
     ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--served-warmup", type=int, default=2000)
     ap.add_argument("--oracle-sample", type=int, default=256,
@@ -938,6 +974,8 @@ def main():
         args.warmup = 3
     if args.sweep:
         return run_sweep(args)
+    if args.batch_probe:
+        return run_batch_probe(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -252,7 +252,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 1u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -274,6 +274,8 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "t2_smem_rows")) d.t2_smem_rows = val;
                 else if (!std::strcmp(key, "seed")) d.seed = val;
                 else if (!std::strcmp(key, "serve_t2")) d.serve_t2 = val;
+                else if (!std::strcmp(key, "batch_wide")) d.batch_wide = val;
+                else if (!std::strcmp(key, "batch_split")) d.batch_split = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -1296,6 +1298,7 @@ struct Bucket {
     double tuned_ms = 0.0;
     bool smem = false;
     std::vector<uint32_t> graphs;
+    std::vector<uint32_t> items;  // work items: graph | part << 16 | parts << 24
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
     LaunchShape shape{};
     uint32_t qcap = 0, fs = 0, groups = 0;
@@ -1330,11 +1333,66 @@ uint32_t words_class(uint32_t n)
     return c;
 }
 
+// Work items of a bucket whose graphs are sorted most expensive first.  A
+// graph expected to cost more than a quarter of a block's fair share of the
+// bucket (its whole cost over `blocks`) is split into k parts of about that
+// size: part j searches the root's children j, j + k, j + 2k, ... (disjoint
+// subtrees of Alg. 4's root), so the heaviest graphs of a batch no longer run
+// on one block while the others idle.  k is capped by about half the
+// expected number of root children (|P \ N(pivot)| ~ n(1 - p)), by
+// kBatchMaxParts and by the kernel's prefix table (kBatchPartWords words per
+// row); subproblems of the outer loop are never split.  Items are sorted by
+// expected cost, largest first.  Returns the most child frames one part
+// queues at its start (0 when nothing is split), which the ring must hold.
+constexpr uint32_t kBatchMaxParts = 64;
+
+uint32_t plan_items(Bucket &bk, mce_graph *const *graphs, const std::vector<double> &cost,
+                    const std::vector<uint32_t> &wp_of, unsigned blocks)
+{
+    double total = 0.0;
+    for (uint32_t i : bk.graphs) total += cost[i];
+    const double target = blocks ? total / (4.0 * blocks) : 0.0;
+    std::vector<std::pair<double, uint32_t>> items;
+    uint32_t frames = 0;
+    for (uint32_t i : bk.graphs) {
+        const mce_graph *g = graphs[i];
+        uint32_t k = 1;
+        if (!g->root && target > 0.0 && cost[i] > 2.0 * target && wp_of[i] <= (uint32_t)kBatchPartWords && g->n > 1) {
+            const double p = std::min(1.0, 2.0 * (double)g->m / ((double)g->n * (g->n - 1.0)));
+            const double children = 0.5 * g->n * (1.0 - p);
+            const double cap = std::min<double>(kBatchMaxParts, std::max(1.0, children));
+            k = (uint32_t)std::min(cap, std::ceil(cost[i] / target));
+        }
+        for (uint32_t j = 0; j < k; ++j) items.push_back({cost[i] / k, i | (j << 16) | (k << 24)});
+        if (k >= 2) frames = std::max(frames, (g->n + k - 1) / k + 1);
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &c) {
+                         return a.first > c.first;
+                     });
+    bk.items.clear();
+    for (auto &it : items) bk.items.push_back(it.second);
+    return frames;
+}
+
+// Launch choice of a batched graph without a tuned one: forced shapes as
+// given; otherwise 512 threads and subtrees of at most two words per lane
+// (one up to 128 vertices), the pattern the autotuner settled on for every
+// words class of the mixed 4,096-graph workload (more, narrower subtrees per
+// block than the plain form's shapes: a batched graph has no device-wide ring
+// to spread its work, so a block needs many subtrees of its own).
 TuneChoice default_choice(uint32_t n, const mce_options &o)
 {
     TuneChoice t;
     pick_shape(n, o, t.G, t.K);
     t.threads = o.threads_per_block ? o.threads_per_block : 256u;
+    if (default_tuning().batch_wide && !o.lanes_per_subtree && !o.words_per_lane) {
+        const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
+        t.K = W <= 4 ? 1 : (W <= 64 ? 2 : 4);
+        t.G = 1;
+        while ((uint32_t)(t.G * t.K) < W) t.G <<= 1;
+        if (!o.threads_per_block) t.threads = kMaxThreads;
+    }
     t.split = o.split_min_p;
     return t;
 }
@@ -1570,14 +1628,15 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         int per_sm = 0;
         if (bk.impl.batch_occupancy((int)threads, smem, &per_sm) != cudaSuccess || per_sm < 1) { rc = MCE_EINVAL; break; }
         unsigned blocks = o.blocks ? o.blocks : (unsigned)(per_sm * sms);
-        blocks = std::min<unsigned>(blocks, (unsigned)bk.graphs.size());
+        const uint32_t part_frames = plan_items(bk, graphs, cost, wp_of, default_tuning().batch_split ? blocks : 0u);
+        blocks = std::min<unsigned>(blocks, (unsigned)bk.items.size());
         bk.shape = LaunchShape{blocks, threads, smem, bk.smem};
         bk.groups = threads / 32 * (32 / bk.G);
-        bk.qcap = next_pow2(std::max<uint64_t>(256, 4ull * bk.groups + 64));
+        bk.qcap = next_pow2(std::max<uint64_t>(256, 4ull * bk.groups + 64 + part_frames));
         if (o.queue_log2) bk.qcap = std::max<uint32_t>(bk.qcap, 1u << o.queue_log2);
         bk.fs = (uint32_t)frame_words((uint32_t)(bk.G * bk.K));
         bk.qstride = batch_region_bytes(bk.qcap, bk.fs);
-        bk.list_off = take(bk.graphs.size() * 4, 16);
+        bk.list_off = take(bk.items.size() * 4, 16);
         bk.next_off = take(4, 128);
         bk.region_off = take(bk.qstride * blocks, 256);
     }
@@ -1623,7 +1682,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
     if (count) e = cudaMemcpyAsync(base + table_off, table.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, s);
     for (const Bucket &bk : buckets)
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + bk.list_off, bk.graphs.data(), bk.graphs.size() * 4, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(base + bk.list_off, bk.items.data(), bk.items.size() * 4, cudaMemcpyHostToDevice, s);
     size_t order_smem = 0;
     if (e == cudaSuccess) e = prepare_order_batch(max_n, max_w, &order_smem);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1657,7 +1716,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
             BatchParams bp{};
             bp.graphs = d_table;
             bp.list = reinterpret_cast<const uint32_t *>(base + bk.list_off);
-            bp.count = (uint32_t)bk.graphs.size();
+            bp.count = (uint32_t)bk.items.size();
             bp.next = reinterpret_cast<unsigned *>(base + bk.next_off);
             bp.qbase = base + bk.region_off;
             bp.qstride = bk.qstride;

@@ -97,6 +97,8 @@ struct Tuning {
     uint32_t t2_smem_rows;  // lane tier on: keep the rows in shared memory (fewer warps) when 1
     uint32_t seed;          // start from every root child as its own queued frame (1) or the root (0)
     uint32_t serve_t2;      // served requests use the lane tier too (its region beside the capped stack)
+    uint32_t batch_wide;    // batched form by default: 512 threads, at most two words per lane (1), or the plain shapes (0)
+    uint32_t batch_split;   // batched form: split the heaviest graphs into root-child parts (1) or not (0)
 };
 
 // The lane tier (second search tier): a frame whose P u X has at most 32
@@ -191,6 +193,10 @@ cudaError_t outer_extract(const BatchGraph *table, uint32_t count, uint32_t max_
                           const uint32_t *pos, const uint32_t *off, const uint32_t *adj, cudaStream_t s);
 // Sum the subproblems' results into out (MCE_OUT_WORDS(n) words, zeroed).
 cudaError_t outer_reduce(const BatchGraph *table, uint32_t count, uint32_t n, uint64_t *out, cudaStream_t s);
+
+// Most words per row of a batched graph that the batch kernel splits into
+// root-child parts (its shared prefix table).
+constexpr int kBatchPartWords = 128;
 
 struct BatchParams {
     const BatchGraph *graphs;

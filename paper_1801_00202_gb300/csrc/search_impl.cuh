@@ -1932,7 +1932,13 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         __syncthreads();
         const unsigned idx = cur;
         if (idx >= bp.count) break;
-        const BatchGraph gd = bp.graphs[bp.list[idx]];
+        // a work item: graph index | part << 16 | parts << 24; a graph split
+        // into parts (parts >= 2) spreads over several blocks, each searching
+        // the root's children t = part, part + parts, ... (independent
+        // subtrees; the root node is counted by part 0)
+        const unsigned item = bp.list[idx];
+        const unsigned part = (item >> 16) & 0xffu, parts = item >> 24;
+        const BatchGraph gd = bp.graphs[item & 0xffffu];
         const uint32_t n = gd.n;
         const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
         uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
@@ -1970,19 +1976,21 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         const unsigned r0 = sub ? 1u : 0u;
         const uint64_t s0 = sub ? mix64((uint64_t)gd.label[gd.rv] + 1u) : 0ull;
 
-        // the root is one node: internal, a leaf (R is maximal) or a dead end
-        for (uint32_t j = threadIdx.x; j < MCE_OUT_WORDS(n); j += blockDim.x) {
-            if (j == MCE_OUT_STATUS) continue;
-            uint64_t v = 0ull;
-            if (j == MCE_OUT_NODES) v = 1ull;
-            if (pne && j == MCE_OUT_INTERNAL) v = 1ull;
-            if (!pne && xne && j == MCE_OUT_DEAD_ENDS) v = 1ull;
+        // the root is one node: internal, a leaf (R is maximal) or a dead end;
+        // the graph's result array starts zeroed (cleared with the batch) and
+        // every part adds to it
+        const bool split = parts >= 2u && !sub;
+        if (threadIdx.x == 0 && (!split || part == 0u)) {
+            unsigned long long *o = reinterpret_cast<unsigned long long *>(gd.out);
+            atomicAdd(o + MCE_OUT_NODES, 1ull);
+            if (pne) atomicAdd(o + MCE_OUT_INTERNAL, 1ull);
+            if (!pne && xne) atomicAdd(o + MCE_OUT_DEAD_ENDS, 1ull);
             if (!pne && !xne) {
-                if (j == MCE_OUT_COUNT || j == MCE_OUT_HIST + r0) v = 1ull;
-                if (j == MCE_OUT_HASH) v = mix64(s0 ^ mix64((uint64_t)r0));
-                if (j == MCE_OUT_MAX_SIZE) v = r0;
+                atomicAdd(o + MCE_OUT_COUNT, 1ull);
+                atomicAdd(o + MCE_OUT_HIST + r0, 1ull);
+                atomicAdd(o + MCE_OUT_HASH, (unsigned long long)mix64(s0 ^ mix64((uint64_t)r0)));
+                atomicMax(o + MCE_OUT_MAX_SIZE, (unsigned long long)r0);
             }
-            gd.out[j] = v;
         }
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
             hv[j] = mix64((uint64_t)(sub ? gd.label[gd.order[j]] : gd.order[j]) + 1u);
@@ -2022,7 +2030,64 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
                 lne = lne || (frames[kFrameHdr + w] & ~gd.ren[(size_t)p0 * WP + w]) != 0u;
         lne = __syncthreads_or(lne) != 0;
         const bool root = valid && pne && lne;
-        for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) seq[j] = (j == 0u && root) ? 1u : j;
+        // a part queues one frame per root child of the part instead of the
+        // root frame: child t branches on the t-th vertex v_t of L = P \ N(p0)
+        // with v_1..v_{t-1} already in X, i.e. the frame (P minus those, X =
+        // those, p0, end = v_t + 1); frames go to slots 1.. (slot 0 keeps the
+        // root frame's layout)
+        unsigned queued = root ? 1u : 0u;
+        if (split) {
+            __shared__ unsigned lpre[kBatchPartWords + 1];
+            const uint32_t *rp0 = gd.ren + (size_t)p0 * WP;
+            if (threadIdx.x == 0) {
+                unsigned acc = 0;
+                for (uint32_t w = 0; w < (uint32_t)WP; ++w) {
+                    lpre[w] = acc;
+                    acc += (unsigned)__popc(frames[kFrameHdr + w] & ~rp0[w]);
+                }
+                lpre[WP] = acc;
+            }
+            __syncthreads();
+            const unsigned nl = lpre[WP];
+            const unsigned mine = nl > part ? (nl - part + parts - 1u) / parts : 0u;
+            for (unsigned j = threadIdx.x; j < mine && j + 1u < bp.qcap; j += blockDim.x) {
+                const unsigned t = part + j * parts;
+                unsigned w = 0;
+                while (w + 1u < (unsigned)WP && lpre[w + 1] <= t) ++w;
+                uint32_t lw = frames[kFrameHdr + w] & ~rp0[w];
+                for (unsigned r = t - lpre[w]; r > 0u; --r) lw &= lw - 1u;
+                const unsigned v = w * 32u + (unsigned)(__ffs(lw) - 1);
+                uint32_t *fr = frames + (size_t)(j + 1u) * bp.fs;
+                for (uint32_t q = 0; q < (uint32_t)WP; ++q) {
+                    const uint32_t pw = frames[kFrameHdr + q];
+                    uint32_t below = 0u;
+                    if (v >= q * 32u + 32u) below = FULL;
+                    else if (v > q * 32u) below = (1u << (v - q * 32u)) - 1u;
+                    const uint32_t x = pw & ~rp0[q] & below;
+                    fr[kFrameHdr + q] = pw & ~x;
+                    fr[kFrameHdr + WP + q] = x;
+                }
+                fr[0] = (p0 & 0xffffu) | ((v + 1u) << 16);
+                fr[1] = 0u;
+                fr[2] = 0u;
+                fr[3] = 0u;
+                fr[4] = 0u;
+            }
+            queued = valid && pne ? min(mine, bp.qcap - 1u) : 0u;
+            if (threadIdx.x == 0 && valid && mine + 1u > bp.qcap)  // the host sizes the ring for this
+                atomicCAS(reinterpret_cast<unsigned long long *>(gd.out + MCE_OUT_STATUS), 0ull,
+                          static_cast<unsigned long long>(static_cast<long long>(MCE_EOVERFLOW)));
+        }
+        // ring state: the root frame is consumer ticket 0 in slot 0; a part's
+        // frames are consumer tickets 1..queued in slots 1..queued (slot 0 is
+        // then free for producer ticket qcap)
+        for (uint32_t j = threadIdx.x; j < bp.qcap; j += blockDim.x) {
+            unsigned sv = j;
+            if (!split && j == 0u && root) sv = 1u;
+            if (split && j == 0u) sv = bp.qcap;
+            if (split && j >= 1u && j <= queued) sv = j + 1u;
+            seq[j] = sv;
+        }
         bool staged = true;
         if (SMEM) staged = stage_rows(srows, gd.ren, (uint32_t)rbytes, mb, phase & 1u);
         ++phase;
@@ -2032,10 +2097,10 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
             frames[1] = r0;
             frames[2] = (uint32_t)s0;
             frames[3] = (uint32_t)(s0 >> 32);
-            ctl->head = 0u;
+            ctl->head = split ? 1u : 0u;
             ctl->abort = 0u;
-            ctl->tail = root ? 1u : 0u;
-            ctl->pending = root ? 1u : 0u;
+            ctl->tail = split ? queued + 1u : (root ? 1u : 0u);
+            ctl->pending = split ? queued : (root ? 1u : 0u);
             ctl->starving = 0u;
             if (!staged) {
                 atomicCAS(reinterpret_cast<unsigned long long *>(gd.out + MCE_OUT_STATUS), 0ull,
