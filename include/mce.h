@@ -364,11 +364,17 @@ int mce_enumerate_part(mce_graph *g, const mce_options *opts, const uint32_t *ch
                        int count_root, mce_result *res);
 
 /* Batched form.  mce_batch_create plans a batch of loaded graphs once:
- * graphs are grouped by subtree shape (lanes x words, chosen per graph like
- * mce_enumerate does, or forced by opts), ordered most expensive first by the
- * expected number of maximal cliques of G(n, m / C(n, 2)), and the whole
- * pipeline (ordering, renumbering, one persistent search launch per shape,
- * each block taking one graph at a time) is captured into a CUDA graph.
+ * graphs are grouped by subtree shape (lanes x words: by default 512 threads
+ * per block and at most two words per lane, or forced by opts, or tuned),
+ * costed by the expected number of maximal cliques of G(n, m / C(n, 2)), and
+ * the whole pipeline (ordering, renumbering, one persistent search launch per
+ * shape, each block taking one work item at a time, most expensive first) is
+ * captured into a CUDA graph.  A work item is a whole graph, or, for a graph
+ * expected to cost more than half a block's fair share of its bucket, one of
+ * k parts of it: part j searches the root children j, j + k, j + 2k, ... of
+ * Alg. 4's root (disjoint subtrees; the root node is counted once), so that
+ * the heaviest graphs spread over several blocks.  Results are the same
+ * either way.
  * mce_batch_launch enqueues that graph on the context stream;
  * mce_batch_results waits and fills res[i] for graphs[i] (hist buffers
  * caller-owned as in mce_enumerate); mce_batch_run does both.  The graphs
@@ -398,6 +404,8 @@ typedef struct {
     uint32_t split_min_p;        /* 0 = by density, 0xffffffff = never      */
     uint32_t tuned;              /* 1 when the choice was measured          */
     double tuned_ms_per_graph;   /* best measured time per graph (tuning)   */
+    uint32_t work_items;         /* graphs plus the extra parts of split ones */
+    uint32_t split_graphs;       /* graphs split into root-child parts        */
 } mce_batch_bucket;
 /* The launch choice of every bucket of a batch: up to cap entries to out,
  * the number of buckets to *count. */

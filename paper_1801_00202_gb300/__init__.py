@@ -59,7 +59,8 @@ class Options(C.Structure):
 class BatchBucket(C.Structure):
     _fields_ = [("words_class", C.c_uint32), ("graphs", C.c_uint32), ("lanes_per_subtree", C.c_uint32),
                 ("words_per_lane", C.c_uint32), ("threads_per_block", C.c_uint32), ("blocks", C.c_uint32),
-                ("split_min_p", C.c_uint32), ("tuned", C.c_uint32), ("tuned_ms_per_graph", C.c_double)]
+                ("split_min_p", C.c_uint32), ("tuned", C.c_uint32), ("tuned_ms_per_graph", C.c_double),
+                ("work_items", C.c_uint32), ("split_graphs", C.c_uint32)]
 
 
 class Peaks(C.Structure):

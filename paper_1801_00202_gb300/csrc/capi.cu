@@ -252,7 +252,7 @@ int cuda_code(cudaError_t e) { return e == cudaSuccess ? MCE_OK : (e == cudaErro
 Tuning mce::default_tuning()
 {
     static const Tuning t = [] {
-        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 1u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 16u, 64u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 4u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -1299,6 +1299,7 @@ struct Bucket {
     bool smem = false;
     std::vector<uint32_t> graphs;
     std::vector<uint32_t> items;  // work items: graph | part << 16 | parts << 24
+    uint32_t split_graphs = 0;
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
     LaunchShape shape{};
     uint32_t qcap = 0, fs = 0, groups = 0;
@@ -1333,10 +1334,10 @@ uint32_t words_class(uint32_t n)
     return c;
 }
 
-// Work items of a bucket whose graphs are sorted most expensive first.  A
-// graph expected to cost more than a quarter of a block's fair share of the
-// bucket (its whole cost over `blocks`) is split into k parts of about that
-// size: part j searches the root's children j, j + k, j + 2k, ... (disjoint
+// Work items of a bucket whose graphs are sorted most expensive first.  With
+// target = the bucket's expected cost / (blocks * div), a graph expected to
+// cost more than twice the target (with div = 4: half a block's fair share)
+// is split into k parts of about the target: part j searches the root's children j, j + k, j + 2k, ... (disjoint
 // subtrees of Alg. 4's root), so the heaviest graphs of a batch no longer run
 // on one block while the others idle.  k is capped by about half the
 // expected number of root children (|P \ N(pivot)| ~ n(1 - p)), by
@@ -1347,11 +1348,11 @@ uint32_t words_class(uint32_t n)
 constexpr uint32_t kBatchMaxParts = 64;
 
 uint32_t plan_items(Bucket &bk, mce_graph *const *graphs, const std::vector<double> &cost,
-                    const std::vector<uint32_t> &wp_of, unsigned blocks)
+                    const std::vector<uint32_t> &wp_of, unsigned blocks, uint32_t div)
 {
     double total = 0.0;
     for (uint32_t i : bk.graphs) total += cost[i];
-    const double target = blocks ? total / (4.0 * blocks) : 0.0;
+    const double target = blocks && div ? total / ((double)div * blocks) : 0.0;
     std::vector<std::pair<double, uint32_t>> items;
     uint32_t frames = 0;
     for (uint32_t i : bk.graphs) {
@@ -1364,7 +1365,10 @@ uint32_t plan_items(Bucket &bk, mce_graph *const *graphs, const std::vector<doub
             k = (uint32_t)std::min(cap, std::ceil(cost[i] / target));
         }
         for (uint32_t j = 0; j < k; ++j) items.push_back({cost[i] / k, i | (j << 16) | (k << 24)});
-        if (k >= 2) frames = std::max(frames, (g->n + k - 1) / k + 1);
+        if (k >= 2) {
+            frames = std::max(frames, (g->n + k - 1) / k + 1);
+            ++bk.split_graphs;
+        }
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &c) {
@@ -1628,7 +1632,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         int per_sm = 0;
         if (bk.impl.batch_occupancy((int)threads, smem, &per_sm) != cudaSuccess || per_sm < 1) { rc = MCE_EINVAL; break; }
         unsigned blocks = o.blocks ? o.blocks : (unsigned)(per_sm * sms);
-        const uint32_t part_frames = plan_items(bk, graphs, cost, wp_of, default_tuning().batch_split ? blocks : 0u);
+        const uint32_t part_frames = plan_items(bk, graphs, cost, wp_of, blocks, default_tuning().batch_split);
         blocks = std::min<unsigned>(blocks, (unsigned)bk.items.size());
         bk.shape = LaunchShape{blocks, threads, smem, bk.smem};
         bk.groups = threads / 32 * (32 / bk.G);
@@ -1652,6 +1656,8 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         bi.split_min_p = bk.split;
         bi.tuned = bk.tuned ? 1u : 0u;
         bi.tuned_ms_per_graph = bk.tuned_ms;
+        bi.work_items = (uint32_t)bk.items.size();
+        bi.split_graphs = bk.split_graphs;
         b->info.push_back(bi);
     }
     b->dbytes = round_up(off, 256);

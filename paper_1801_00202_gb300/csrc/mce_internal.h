@@ -98,7 +98,7 @@ struct Tuning {
     uint32_t seed;          // start from every root child as its own queued frame (1) or the root (0)
     uint32_t serve_t2;      // served requests use the lane tier too (its region beside the capped stack)
     uint32_t batch_wide;    // batched form by default: 512 threads, at most two words per lane (1), or the plain shapes (0)
-    uint32_t batch_split;   // batched form: split the heaviest graphs into root-child parts (1) or not (0)
+    uint32_t batch_split;   // batched form: parts of about 1/(blocks * batch_split) of a bucket's cost (0: no split)
 };
 
 // The lane tier (second search tier): a frame whose P u X has at most 32

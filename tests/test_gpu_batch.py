@@ -64,6 +64,33 @@ def test_mixed_batch_matches_oracle(ctx, mce, mode):
         g.free()
 
 
+@pytest.mark.parametrize("mode", ["greedy", "tx", "tomita", "nx"])
+def test_heavy_graphs_split_into_root_child_parts(ctx, mce, mode):
+    # two heavy graphs among light ones: the plan splits each heavy graph into
+    # parts that search every k-th root child on different blocks (the dense
+    # one has only a few root children, so few parts); the parts add up to
+    # the oracle's result and the plan replays with the same result
+    specs = [(150, synth.gnp(150, 0.5, 300)), (60, synth.gnp(60, 0.8, 301))] + \
+            [(40, synth.gnp(40, 0.3, 310 + i)) for i in range(30)]
+    graphs = [ctx.load_edges(n, uv) for n, uv in specs]
+    b = mce.Batch(ctx, graphs, mce.options(pivot=mode))
+    try:
+        info = b.buckets()
+        assert sum(x["split_graphs"] for x in info) == 2
+        assert sum(x["work_items"] for x in info) > len(specs) + 2
+        assert sum(x["graphs"] for x in info) == len(specs)
+        first = b.run()
+        for (n, uv), got in zip(specs, first):
+            _check(got, n, uv, mode)
+        again = b.run()
+        assert [(r["count"], r["hash"], r["nodes"]) for r in again] == \
+            [(r["count"], r["hash"], r["nodes"]) for r in first]
+    finally:
+        b.close()
+        for g in graphs:
+            g.free()
+
+
 def test_batch_equals_alone_and_replays(ctx, mce):
     specs = [(int(n), synth.gnp(int(n), p, 100 + i)) for i, (n, p) in
              enumerate([(40, 0.7), (80, 0.5), (150, 0.4), (260, 0.3), (400, 0.2), (500, 0.15)] * 6)]
