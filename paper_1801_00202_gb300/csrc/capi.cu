@@ -174,7 +174,7 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     // gets fewer warps so that they fit, or they are read from L2.
     const Tuning tu = default_tuning();
     const bool t2 = !c.list && G >= 2 && tu.t2_p != 0 && (stack_cap == ~(size_t)0 || tu.serve_t2);
-    const size_t t2w = t2 ? t2_warp_bytes(tu.t2_levels) : 0;
+    const size_t t2w = t2 ? t2_warp_bytes(tu.t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY) : 0;
     auto fits = [&](bool rows_smem, unsigned threads) {
         return round_up(search_smem(n, c.wp, rows_smem, c.list), 16) + (size_t)(threads / 32) * t2w <= limit;
     };
@@ -1618,7 +1618,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         // an SM
         const Tuning tu = default_tuning();
         if (bk.G >= 2 && tu.t2_p != 0u) {
-            const size_t off = round_up(base, 16), t2b = (size_t)(threads / 32) * t2_warp_bytes(tu.t2_levels);
+            const size_t off = round_up(base, 16), t2b = (size_t)(threads / 32) * t2_warp_bytes(tu.t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY);
             if (off + t2b <= slimit) {
                 bk.t2_offset = (uint32_t)off;
                 bk.t2_levels = tu.t2_levels;

@@ -107,13 +107,16 @@ struct Tuning {
 // A[row][lane] (u32), the positions of their local vertices pos[v][lane]
 // (u16), and t2_levels explicit-stack levels of six words per lane
 // [level][field][lane] (P, X, L, |R|, S low, S high).
-// After them, 512 bytes of scratch for the group search's parallel pivot
-// scoring (each lane's words of P').
+// After them, for the pivot rules that score candidates (GreedyBBTX/NX,
+// TomitaBB), 512 bytes of scratch for the group search's parallel pivot
+// scoring (each lane's words of P'); GreedyBB needs none, so its blocks keep
+// that room (on 1,000 vertices with rows in shared memory: a quarter more
+// warps).
 constexpr int kT2Fields = 6;
 constexpr int kPivotScratchWords = 128;
-__host__ __device__ inline size_t t2_warp_bytes(uint32_t levels)
+__host__ __device__ inline size_t t2_warp_bytes(uint32_t levels, bool scoring)
 {
-    return 32 * 32 * 4 + 32 * 32 * 2 + (size_t)levels * kT2Fields * 32 * 4 + kPivotScratchWords * 4;
+    return 32 * 32 * 4 + 32 * 32 * 2 + (size_t)levels * kT2Fields * 32 * 4 + (scoring ? kPivotScratchWords * 4 : 0);
 }
 
 struct SearchParams {

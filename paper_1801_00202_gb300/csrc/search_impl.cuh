@@ -1058,7 +1058,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     uint32_t t2_spill[32][kT2Fields];
     const unsigned t2p = T2 ? min(prm.t2_max_p, th.share_local) : 0u;
     {
-        unsigned char *wb = t2_smem + (size_t)(threadIdx.x >> 5) * t2_warp_bytes(prm.t2_levels);
+        unsigned char *wb = t2_smem + (size_t)(threadIdx.x >> 5) * t2_warp_bytes(prm.t2_levels, PIVOT != MCE_PIVOT_GREEDY);
         t2m.A = reinterpret_cast<uint32_t *>(wb);
         t2m.pos = reinterpret_cast<uint16_t *>(wb + 32 * 32 * 4);
         t2m.stk = reinterpret_cast<uint32_t *>(wb + 32 * 32 * 4 + 32 * 32 * 2);
