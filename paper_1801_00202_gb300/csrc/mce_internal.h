@@ -42,10 +42,11 @@ struct LocalHdr {
                           // one unit of Ctl::pending while this is non-zero
     unsigned starving;    // this block is counted in Ctl::starving
     unsigned poller;      // a warp of this block is polling the global ring
-    unsigned done;        // the search is over
+    unsigned done;        // the search is over (1) or aborted (2)
     unsigned refreshing;  // a warp is refreshing the cached global state
     // cached global state (refreshed every few microseconds)
-    unsigned g_head, g_tail, g_starving, g_abort;
+    unsigned g_head, g_tail, g_starving;
+    unsigned spare;       // unused (keeps the stamp 8-byte aligned)
     unsigned long long stamp;
     unsigned trace_n;     // timeline records written by this block
     unsigned t2_busy;     // lanes of the block holding a lane-tier subproblem

@@ -153,25 +153,27 @@ __device__ __forceinline__ void set_status(uint64_t *out, Ctl *ctl, int code)
 // seq == ticket is free for producer `ticket`, seq == ticket + 1 holds the
 // frame for consumer `ticket`).
 
+// Reserve a producer ticket: check the room left -- producer tickets at
+// most qcap - margin ahead of the consumers', margin = the groups that can
+// reserve at once (one ticket each) -- and take the ticket with one
+// fetch-and-add, so producers race no compare-and-swap either.  The room
+// check puts the ticket's slot behind a consumer ticket already claimed, so
+// the slot is free as soon as that frame has been taken (microseconds;
+// waited for, with a bound).  On false the caller keeps its frame; a ticket
+// taken but never filled (the bounded wait ran out, or the search aborted)
+// only leaves its consumer idle.
 __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
-                                               unsigned long long *fails)
+                                               unsigned margin)
 {
-    unsigned pos = ld_relaxed(&ctl->tail);
-    for (unsigned t = 0; t < kCasTries; ++t) {
-        unsigned s = ld_acquire(&seq[pos & mask]);
-        int dif = (int)(s - pos);
-        if (dif == 0) {
-            unsigned prev = atomicCAS(&ctl->tail, pos, pos + 1);
-            if (prev == pos) { ticket = pos; return true; }
-            atomicAdd(fails, 1ull);
-            pos = prev;
-        } else if (dif < 0) {
-            return false;  // full
-        } else {
-            pos = ld_relaxed(&ctl->tail);
-        }
+    const unsigned hd = ld_relaxed(&ctl->head), tl = ld_relaxed(&ctl->tail);
+    if ((int)(tl - hd) >= (int)(mask + 1u) - (int)margin) return false;
+    const unsigned tk = atomicAdd(&ctl->tail, 1u);
+    for (unsigned t = 0; ld_acquire(&seq[tk & mask]) != tk; ++t) {
+        if (t >= (kCasTries << 8) || ld_relaxed(&ctl->abort)) return false;
+        __nanosleep(32);
     }
-    return false;
+    ticket = tk;
+    return true;
 }
 
 __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
@@ -193,6 +195,37 @@ __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned 
         }
     }
     return false;
+}
+
+// Room kept free in a frame ring for producers that reserve at once: every
+// group of the launch on the device-wide ring (the plain form sizes the ring
+// at four frames per group and more), the block's groups on a block-private
+// ring (batched form).
+template <int G>
+__device__ __forceinline__ unsigned push_margin(const SearchParams &prm)
+{
+    const unsigned block_groups = (blockDim.x >> 5) * (32u / G);
+    return (prm.total_groups > block_groups ? prm.total_groups : block_groups) + 32u;
+}
+
+// Claim up to `want` consecutive consumer tickets of the device-wide ring
+// with one fetch-and-add: first .. first + k - 1.  Only frames seen in the
+// ring are claimed, so claimers never race a compare-and-swap on the head
+// (under a compare-and-swap, most of the idle blocks' attempts failed and
+// were retried, and the ring's head was the search's bottleneck); two
+// claimers that saw the same frames can take tickets past the producers'.
+// A claimed ticket is the claimer's alone: its frame is taken once the
+// producer has published it (seq == ticket + 1), or never if the search ends
+// first -- the search ends only when no frame is queued or held anywhere
+// (pending == 0), so no published frame is ever left behind.  Returns k.
+__device__ __forceinline__ unsigned q_claim(Ctl *ctl, unsigned want, unsigned &first)
+{
+    const unsigned h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
+    const int avail = (int)(t - h);
+    if (avail <= 0) return 0u;
+    const unsigned k = min(want, (unsigned)avail);
+    first = atomicAdd(&ctl->head, k);
+    return k;
 }
 
 // Take up to `want` consecutive frames (the ring's oldest) with one ticket
@@ -467,7 +500,6 @@ __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned grou
         q.h->g_head = 0u;
         q.h->g_tail = 0u;
         q.h->g_starving = 0u;
-        q.h->g_abort = 0u;
         q.h->stamp = 0ull;
         q.h->trace_n = 0u;
         q.h->t2_busy = 0u;
@@ -552,7 +584,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
             if (!got) atomicSub(&lq.h->bwork, 1u);
         } else {
             atomicAdd(&prm.ctl->pending, 1u);
-            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket, cn.diag + kDiagCasFail) ? 1u : 0u;
+            got = q_reserve_push(prm.ctl, prm.seq, prm.qcap - 1u, ticket, push_margin<G>(prm)) ? 1u : 0u;
             if (got) cn.note(kDiagGpush);
             if (!got) atomicSub(&prm.ctl->pending, 1u);
         }
@@ -846,7 +878,7 @@ __device__ __forceinline__ bool push_global(const Grp<G, K> &g, const SearchPara
     unsigned ticket = 0, got = 0;
     if (pred && g.leader()) {
         atomicAdd(&prm.ctl->pending, 1u);
-        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket, cn.diag + kDiagCasFail) ? 1u : 0u;
+        got = q_reserve_push(prm.ctl, prm.seq, qmask, ticket, push_margin<G>(prm)) ? 1u : 0u;
         if (got) cn.note(kDiagGpush);
         if (!got) atomicSub(&prm.ctl->pending, 1u);
     }
@@ -1037,6 +1069,10 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
     bool lempty = true;  // the current frame's branching set is exhausted
     bool poller = false;
     unsigned gq = 0;  // global ring length last seen
+    // a claimed ticket of the device-wide ring whose frame this (idle) group
+    // takes once it is published
+    bool held = false;
+    unsigned hticket = 0;
     // Clique listing (ListParams): this group's index, the |R| of the frame
     // it took last, and (leader) the chunk it appends records to.
     constexpr bool list = LIST;
@@ -1394,7 +1430,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (busy_b == 0u && ld && !t2any) break;
             const unsigned lqueued = lt - lh;
             unsigned ticket = 0, got = 0;
-            if (!work && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, ticket) ? 1u : 0u;
+            if (!work && !held && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, ticket) ? 1u : 0u;
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
             if (got) {
@@ -1435,7 +1471,11 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         // read by the block's polling warp (an all-idle warp) or, at most
         // every tune.refresh_ns, by one busy warp, and cached in shared memory.
         const unsigned busy2 = __ballot_sync(FULL, work);
-        if (busy2 == 0u || (it & (prm.tune.global_check - 1u)) == 0u) {
+        const bool anyheld = __ballot_sync(FULL, held) != 0u;
+        const bool periodic = busy2 == 0u || (it & (prm.tune.global_check - 1u)) == 0u;
+        // a held ticket is looked at every eighth iteration of a warp whose
+        // other groups are busy (each look is a round trip to L2)
+        if (periodic || (anyheld && (it & 7u) == 0u)) {
             unsigned head = 0, tail = 0, pend = 1, starving = 0, ab = 0, lh = 0, lt = 0, done = 0;
             bool pol = poller;
             if (g.lane == 0) {
@@ -1466,15 +1506,15 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     vst(&lq.h->g_head, head);
                     vst(&lq.h->g_tail, tail);
                     vst(&lq.h->g_starving, starving);
-                    vst(&lq.h->g_abort, ab);
-                    if (ab || pend == 0u) vst(&lq.h->done, 1u);
+                    if (ab || pend == 0u) vst(&lq.h->done, ab ? 2u : 1u);
                     *reinterpret_cast<volatile unsigned long long *>(&lq.h->stamp) = now;
                     if (prm.trace) {
                         const unsigned ti = atomicAdd(&lq.h->trace_n, 1u);
                         if (ti < prm.trace_per_block) {
                             const unsigned groups = prm.total_groups / gridDim.x;
                             const unsigned busy = groups - min(groups, vld(&lq.h->idle));
-                            const unsigned qg = min(tail - head, 65535u), sv = min(starving, 65535u);
+                            const unsigned qg = (int)(tail - head) > 0 ? min(tail - head, 65535u) : 0u;
+                            const unsigned sv = min(starving, 65535u);
                             unsigned long long *rec = prm.trace + 2ull * ((size_t)blockIdx.x * prm.trace_per_block + ti);
                             rec[0] = now;
                             rec[1] = (unsigned long long)busy | ((unsigned long long)min(vld(&lq.h->t2_busy), 65535u) << 16) |
@@ -1487,7 +1527,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                     head = vld(&lq.h->g_head);
                     tail = vld(&lq.h->g_tail);
                     starving = vld(&lq.h->g_starving);
-                    ab = vld(&lq.h->g_abort);
+                    ab = vld(&lq.h->done) == 2u ? 1u : 0u;
                 }
                 done = vld(&lq.h->done);
             }
@@ -1503,7 +1543,8 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             done = __shfl_sync(FULL, done, 0);
             if (ab) break;
             if (busy2 == 0u && done && !t2any) break;
-            const unsigned queued = tail - head;
+            // (claimed tickets can run ahead of the producers': nothing queued)
+            const unsigned queued = (int)(tail - head) > 0 ? tail - head : 0u;
             gq = queued;
 
             // An idle group takes a global frame when its block's ring is
@@ -1517,7 +1558,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             // of the warp's asking groups with one ticket advance.
             unsigned ticket = 0, got = 0;
             const bool ring_shared = prm.total_groups > (blockDim.x >> 5) * (32u / G);
-            const bool ask = !work && queued != 0u && lt == lh && (poller || !ring_shared) && g.leader();
+            const bool ask = !work && !held && queued != 0u && lt == lh && (poller || !ring_shared) && g.leader();
             const unsigned askers = __ballot_sync(FULL, ask);
             if (!ring_shared) {
                 if (ask) {
@@ -1529,19 +1570,31 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 unsigned first = 0u, k = 0u;
                 if (g.lane == lead) {
                     cn.note(kDiagGtry);
-                    k = q_reserve_pop_many(ctl, prm.seq, qmask, min(4u, (unsigned)__popc(askers)), first,
-                                           cn.diag + kDiagCasFail, prm.tune.pop_tries);
+                    k = q_claim(ctl, min(4u, (unsigned)__popc(askers)), first);
                 }
                 k = __shfl_sync(FULL, k, (int)lead);
                 first = __shfl_sync(FULL, first, (int)lead);
                 const unsigned rank = (unsigned)__popc(askers & ((1u << g.lane) - 1u));
                 if (ask && rank < k) {
-                    got = 1u;
-                    ticket = first + rank;
+                    held = true;
+                    hticket = first + rank;
                 }
             }
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
+            held = g.from_leader(held ? 1u : 0u) != 0u;
+            hticket = g.from_leader(hticket);
+            if (ring_shared && __ballot_sync(FULL, held) != 0u) {
+                // a held ticket's frame, once its producer has published it
+                unsigned rdy = 0u;
+                if (held && g.leader()) rdy = ld_acquire(&prm.seq[hticket & qmask]) == hticket + 1u ? 1u : 0u;
+                rdy = g.from_leader(rdy);
+                if (rdy) {
+                    got = 1u;
+                    ticket = hticket;
+                    held = false;
+                }
+            }
             if (got) {
                 __threadfence();
                 const uint32_t *fr = prm.frames + (size_t)(ticket & qmask) * prm.fs;
@@ -1578,7 +1631,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             }
 
             // busy groups feed starving blocks
-            const bool hungry = work && !got && starving > queued;
+            const bool hungry = periodic && work && !got && starving > queued;
             // with half the blocks starving (the search is draining), so are
             // smaller frames
             const int gmin = 2u * starving > gridDim.x ? (int)min(th.share_global, prm.tune.share_tail)
@@ -1603,7 +1656,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
                 // the block ring and may sleep longer (fewer issue slots taken
                 // from the busy warps of the SM)
                 __nanosleep(backoff);
-                const unsigned cap = poller ? 1024u : prm.tune.idle_sleep_ns;
+                const unsigned cap = (poller || anyheld) ? 1024u : prm.tune.idle_sleep_ns;
                 backoff = backoff < cap ? backoff * 2u : cap;
                 continue;
             }
