@@ -167,8 +167,12 @@ typedef struct {
                                   utilisation = busy / (groups x duration)   */
 #define MCE_OUT_GROUPS    11   /* subtree groups of the launch               */
 #define MCE_OUT_GPUSH     12   /* frames published to the device-wide queue  */
-#define MCE_OUT_GTRY      13   /* attempts to take a frame from it           */
-#define MCE_OUT_CAS_FAIL  14   /* lost compare-and-swap races on its tickets */
+#define MCE_OUT_GTRY      13   /* claims of frames from it (one fetch-and-add
+                                  each, for up to four frames)              */
+#define MCE_OUT_CAS_FAIL  14   /* lost compare-and-swap races on ticket
+                                  counters (block-private rings of the
+                                  batched form; the device-wide queue
+                                  takes tickets by fetch-and-add)           */
 #define MCE_OUT_LANE_TASKS 15  /* subtrees handed to single lanes (frames
                                   whose P u X has at most 32 vertices,
                                   searched with 32-bit local sets)          */

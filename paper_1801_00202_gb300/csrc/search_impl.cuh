@@ -21,8 +21,10 @@
 //    ring in shared memory, which busy groups of the block refill by giving
 //    away the front half of their shallowest branching set; blocks whose
 //    groups are idle with an empty ring count as starving, one idle warp per
-//    block polls the global ring (a bounded MPMC ring in global memory), and
-//    busy groups feed that ring while starving blocks outnumber its frames.
+//    block polls the global ring (a bounded MPMC ring in global memory whose
+//    tickets are taken by fetch-and-add at both ends, never by a contended
+//    compare-and-swap), and busy groups feed that ring while starving blocks
+//    outnumber its frames.
 //    Cutting a branching set L into a front part L1 (given) and the rest as
 //    (P, X, end = first kept element) and (P \ L1, X u L1, end) reproduces
 //    exactly the sequential P/X updates of Alg. 4, so node counts do not
@@ -176,6 +178,9 @@ __device__ __forceinline__ bool q_reserve_push(Ctl *ctl, unsigned *seq, unsigned
     return true;
 }
 
+// Take the oldest published frame of a block-private ring (batched form:
+// the only contenders are the block's own groups, so a compare-and-swap on
+// the head is cheap there).
 __device__ __forceinline__ bool q_reserve_pop(Ctl *ctl, unsigned *seq, unsigned mask, unsigned &ticket,
                                               unsigned long long *fails, unsigned tries = kCasTries)
 {
@@ -226,33 +231,6 @@ __device__ __forceinline__ unsigned q_claim(Ctl *ctl, unsigned want, unsigned &f
     const unsigned k = min(want, (unsigned)avail);
     first = atomicAdd(&ctl->head, k);
     return k;
-}
-
-// Take up to `want` consecutive frames (the ring's oldest) with one ticket
-// advance: consumer tickets first .. first + k - 1.  Returns k (0 when the
-// ring is empty or the tries ran out).
-__device__ __forceinline__ unsigned q_reserve_pop_many(Ctl *ctl, unsigned *seq, unsigned mask, unsigned want,
-                                                       unsigned &first, unsigned long long *fails, unsigned tries)
-{
-    unsigned pos = ld_relaxed(&ctl->head);
-    for (unsigned t = 0; t < tries; ++t) {
-        unsigned k = 0;
-        while (k < want && ld_acquire(&seq[(pos + k) & mask]) == pos + k + 1u) ++k;
-        if (k == 0) {
-            const int dif = (int)(ld_acquire(&seq[pos & mask]) - (pos + 1));
-            if (dif < 0) return 0u;  // empty
-            pos = ld_relaxed(&ctl->head);
-            continue;
-        }
-        const unsigned prev = atomicCAS(&ctl->head, pos, pos + k);
-        if (prev == pos) {
-            first = pos;
-            return k;
-        }
-        atomicAdd(fails, 1ull);
-        pos = prev;
-    }
-    return 0u;
 }
 
 // ---------------------------------------------------------------------------
