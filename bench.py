@@ -88,10 +88,13 @@ def measure_peaks(mce, device: int) -> dict:
     pk = mce.mce_measure_peaks(device)
     ALU_PEAK_OPS = pk["lop3_lane_ops_per_s"]
     SMEM_PEAK_BPS = pk["lds_bytes_per_s"]
-    PEAKS = {"source": "measured: mce_measure_peaks (LOP3 / POPC lane-op and LDS.128 microbenchmarks, "
-                       "CUDA events, all SMs)",
+    PEAKS = {"source": "measured: mce_measure_peaks (LOP3 / POPC lane-op, LDS.128 and warp-collective "
+                       "microbenchmarks, CUDA events, all SMs)",
              "lop3_tops": pk["lop3_lane_ops_per_s"] / 1e12, "popc_tops": pk["popc_lane_ops_per_s"] / 1e12,
-             "lds_gbs": pk["lds_bytes_per_s"] / 1e9, "sm_count": pk["sm_count"],
+             "lds_gbs": pk["lds_bytes_per_s"] / 1e9,
+             "ballot_g_warp_ops": pk["ballot_warp_ops_per_s"] / 1e9,
+             "shfl_g_warp_ops": pk["shfl_warp_ops_per_s"] / 1e9,
+             "redux_g_warp_ops": pk["redux_warp_ops_per_s"] / 1e9, "sm_count": pk["sm_count"],
              "sm_clock_max_mhz": pk["sm_clock_max_khz"] / 1e3,
              "derived_alu_tops": DERIVED_ALU_OPS / 1e12, "derived_lds_gbs": DERIVED_SMEM_BPS / 1e9}
     return PEAKS

@@ -456,10 +456,11 @@ int mce_trace_enable(void *d_buf, uint64_t bytes);
 
 /* Throughput of the resources that bound the search (it does no dense
  * contraction and, with the rows staged, no HBM traffic): LOP3 (the AND,
- * ANDNOT, OR of set words) and POPC lane operations per second, and 128-bit
- * shared-memory load bandwidth, each measured by a microbenchmark kernel
- * with eight independent chains per thread on every SM of `device`, timed
- * with CUDA events (about 0.1 s in all).  Also the SM count and the maximum
+ * ANDNOT, OR of set words) and POPC lane operations per second, 128-bit
+ * shared-memory load bandwidth, and the warp collectives of every node
+ * (ballot, shuffle, max reduction), each measured by a microbenchmark
+ * kernel with eight independent chains per thread on every SM of `device`,
+ * timed with CUDA events (about 0.1 s in all).  Also the SM count and the maximum
  * SM clock from the device attributes.  Allocates a few bytes of device
  * memory; changes no clock or other device setting. */
 typedef struct {
@@ -469,6 +470,11 @@ typedef struct {
     double ms_lop3, ms_popc, ms_lds;   /* per timed launch                  */
     uint32_t sm_count;
     uint32_t sm_clock_max_khz;
+    /* warp collectives, in warp instructions per second (all 32 lanes):
+     * __ballot_sync, __shfl_xor_sync, __reduce_max_sync (redux.sync)     */
+    double ballot_warp_ops_per_s;
+    double shfl_warp_ops_per_s;
+    double redux_warp_ops_per_s;
 } mce_peaks;
 int mce_measure_peaks(int device, mce_peaks *out);
 

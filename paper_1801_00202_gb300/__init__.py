@@ -66,7 +66,9 @@ class BatchBucket(C.Structure):
 class Peaks(C.Structure):
     _fields_ = [("lop3_lane_ops_per_s", C.c_double), ("popc_lane_ops_per_s", C.c_double),
                 ("lds_bytes_per_s", C.c_double), ("ms_lop3", C.c_double), ("ms_popc", C.c_double),
-                ("ms_lds", C.c_double), ("sm_count", C.c_uint32), ("sm_clock_max_khz", C.c_uint32)]
+                ("ms_lds", C.c_double), ("sm_count", C.c_uint32), ("sm_clock_max_khz", C.c_uint32),
+                ("ballot_warp_ops_per_s", C.c_double), ("shfl_warp_ops_per_s", C.c_double),
+                ("redux_warp_ops_per_s", C.c_double)]
 
 
 class Result(C.Structure):

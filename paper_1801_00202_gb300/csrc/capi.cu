@@ -1390,12 +1390,12 @@ uint32_t plan_items(Bucket &bk, mce_graph *const *graphs, const std::vector<doub
 // words class of the mixed 4,096-graph workload (more, narrower subtrees per
 // block than the plain form's shapes: a batched graph has no device-wide ring
 // to spread its work, so a block needs many subtrees of its own).
-TuneChoice default_choice(uint32_t n, const mce_options &o)
+TuneChoice default_choice(uint32_t n, const mce_options &o, bool wide)
 {
     TuneChoice t;
     pick_shape(n, o, t.G, t.K);
     t.threads = o.threads_per_block ? o.threads_per_block : 256u;
-    if (default_tuning().batch_wide && !o.lanes_per_subtree && !o.words_per_lane) {
+    if (wide && default_tuning().batch_wide && !o.lanes_per_subtree && !o.words_per_lane) {
         const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
         t.K = W <= 4 ? 1 : (W <= 64 ? 2 : 4);
         t.G = 1;
@@ -1408,9 +1408,15 @@ TuneChoice default_choice(uint32_t n, const mce_options &o)
 
 // Plan and capture a batch with the launch choice of every words class
 // given in `choice` (classes not in it: the defaults).
+// subproblems: a batch of the outer loop's many small subproblems (Alg. 3):
+// untuned graphs take the plain form's shapes instead of default_choice's
+// wide ones, and no lane tier (on G(10000, p) with p = 0.01 / 0.03 the lane
+// tier made the batch 5.8 / 19.5 ms against 3.9 / 17.1 ms without it: a
+// subproblem's frames are small from the start, and the tier's region costs
+// the block its stack levels in shared memory).
 int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
                       const std::map<uint32_t, TuneChoice> &choice, mce_batch **out,
-                      cudaStream_t stream = nullptr);
+                      cudaStream_t stream = nullptr, bool subproblems = false);
 
 // Milliseconds of one launch of a batch planned with `choice` (the second of
 // two launches), or a negative value if it cannot run.
@@ -1531,7 +1537,8 @@ extern "C" int mce_batch_create(mce_ctx *ctx, mce_graph *const *graphs, uint32_t
 namespace {
 
 int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, const mce_options &o,
-                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out, cudaStream_t stream)
+                      const std::map<uint32_t, TuneChoice> &choice, mce_batch **out, cudaStream_t stream,
+                      bool subproblems)
 {
     *out = nullptr;
     int dev = 0, sms = 0, optin = 0;
@@ -1564,7 +1571,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         const uint32_t W = std::max<uint32_t>(1, (g->n + 31) / 32);
         const uint32_t wc = words_class(g->n);
         auto it = choice.find(wc);
-        const TuneChoice t = it != choice.end() ? it->second : default_choice(g->n, o);
+        const TuneChoice t = it != choice.end() ? it->second : default_choice(g->n, o, !subproblems);
         const int G = t.G, K = t.K;
         if ((uint32_t)(G * K) < W || !impl_for(G, K, false, (int)o.pivot_mode).run) { delete b; return MCE_EINVAL; }
         size_t bi = 0;
@@ -1622,7 +1629,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
         // then at most 56 KB of stack per block, so that several blocks share
         // an SM
         const Tuning tu = default_tuning();
-        if (bk.G >= 2 && tu.t2_p != 0u) {
+        if (bk.G >= 2 && tu.t2_p != 0u && !subproblems) {
             const size_t off = round_up(base, 16), t2b = (size_t)(threads / 32) * t2_warp_bytes(tu.t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY);
             if (off + t2b <= slimit) {
                 bk.t2_offset = (uint32_t)off;
@@ -1870,7 +1877,8 @@ int enumerate_outer(mce_graph *g, const mce_options &o, mce_result *res, std::ch
     mce_batch *b = nullptr;
     mce_options bo = o;
     bo.flags &= ~(MCE_OUTER | MCE_AUTOTUNE | MCE_ORDER_IDENTITY);
-    if (e == cudaSuccess) rc = batch_create_impl(ctx, ptrs.data(), n, bo, std::map<uint32_t, TuneChoice>{}, &b);
+    if (e == cudaSuccess)
+        rc = batch_create_impl(ctx, ptrs.data(), n, bo, std::map<uint32_t, TuneChoice>{}, &b, nullptr, true);
     uint64_t *d_out = nullptr;
     const size_t obytes = MCE_OUT_WORDS(n) * 8;
     if (e == cudaSuccess && rc == MCE_OK) rc = dalloc(ctx, (void **)&d_out, obytes, s);

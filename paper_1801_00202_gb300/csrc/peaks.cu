@@ -89,6 +89,57 @@ __global__ void __launch_bounds__(kThreads) lds_kernel(uint32_t seed, uint32_t *
     if ((x0 ^ x1) == 0x12345678u) sink[blockIdx.x] = x0;
 }
 
+// Warp collectives the search issues per node (first vertex of a set: a
+// ballot; group sums and broadcasts: shuffles; the pivot argmax: a packed
+// max reduction).  8 chains x 8 collectives per loop trip, each chain's
+// operand changed by one LOP3 between collectives; counted as collectives.
+constexpr int kCollIters = 1024;
+__global__ void __launch_bounds__(kThreads) ballot_kernel(uint32_t seed, uint32_t *sink)
+{
+    uint32_t a[8];
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = seed * (threadIdx.x + 1u) + (uint32_t)i * 0x9e3779b9u;
+    for (int it = 0; it < kCollIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = __ballot_sync(0xffffffffu, (a[i] >> lane) & 1u) ^ (uint32_t)(it + i);
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= a[i];
+    if (x == 0x12345678u) sink[blockIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(kThreads) shfl_kernel(uint32_t seed, uint32_t *sink)
+{
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = seed * (threadIdx.x + 1u) + (uint32_t)i * 0x9e3779b9u;
+    for (int it = 0; it < kCollIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = __shfl_xor_sync(0xffffffffu, a[i], (it + i) & 31) ^ (uint32_t)it;
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= a[i];
+    if (x == 0x12345678u) sink[blockIdx.x] = x;
+}
+
+__global__ void __launch_bounds__(kThreads) redux_kernel(uint32_t seed, uint32_t *sink)
+{
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = seed * (threadIdx.x + 1u) + (uint32_t)i * 0x9e3779b9u;
+    for (int it = 0; it < kCollIters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = __reduce_max_sync(0xffffffffu, a[i] ^ (threadIdx.x * (uint32_t)(it + 1)));
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= a[i];
+    if (x == 0x12345678u) sink[blockIdx.x] = x;
+}
+
 template <typename F>
 int time_kernel(F launch, cudaStream_t s, double *ms)
 {
@@ -136,6 +187,13 @@ extern "C" int mce_measure_peaks(int device, mce_peaks *out)
         rc = time_kernel([&] { popc_kernel<<<blocks, kThreads, 0, s>>>(0x2545f491u, sink); }, s, &ms_popc);
     if (rc == MCE_OK)
         rc = time_kernel([&] { lds_kernel<<<blocks, kThreads, 0, s>>>(0x2545f491u, sink); }, s, &ms_lds);
+    double ms_ballot = 0, ms_shfl = 0, ms_redux = 0;
+    if (rc == MCE_OK)
+        rc = time_kernel([&] { ballot_kernel<<<blocks, kThreads, 0, s>>>(0x2545f491u, sink); }, s, &ms_ballot);
+    if (rc == MCE_OK)
+        rc = time_kernel([&] { shfl_kernel<<<blocks, kThreads, 0, s>>>(0x2545f491u, sink); }, s, &ms_shfl);
+    if (rc == MCE_OK)
+        rc = time_kernel([&] { redux_kernel<<<blocks, kThreads, 0, s>>>(0x2545f491u, sink); }, s, &ms_redux);
     if (rc == MCE_OK) {
         const double lanes = (double)blocks * kThreads;
         out->lop3_lane_ops_per_s = lanes * kIters * 16.0 / (ms_lop * 1e-3);
@@ -146,6 +204,10 @@ extern "C" int mce_measure_peaks(int device, mce_peaks *out)
         out->ms_lop3 = ms_lop;
         out->ms_popc = ms_popc;
         out->ms_lds = ms_lds;
+        const double warps = (double)blocks * (kThreads / 32);
+        out->ballot_warp_ops_per_s = warps * kCollIters * 8.0 / (ms_ballot * 1e-3);
+        out->shfl_warp_ops_per_s = warps * kCollIters * 8.0 / (ms_shfl * 1e-3);
+        out->redux_warp_ops_per_s = warps * kCollIters * 8.0 / (ms_redux * 1e-3);
     }
     if (sink) cudaFree(sink);
     if (s) cudaStreamDestroy(s);

@@ -124,19 +124,24 @@ __device__ __forceinline__ void order_body(uint32_t n, uint32_t w, const uint32_
 }
 
 // The same order for one graph with the whole block (eight warps): thread t
-// owns the keys of vertices t, t + 256, ... (KP of them).  A round takes each
-// warp's maximum key (__reduce_max_sync), the block maximum through a
-// double-buffered slot per warp in shared memory (one barrier per round: a
-// warp cannot reach round i + 2's write before every warp has passed round
-// i + 1's barrier, after its reads of round i), places that vertex and
-// decrements the keys of its remaining neighbours.
+// owns the keys of vertices t, t + 256, ... (KP of them).  A round finds the
+// two largest keys of the block (each warp's two largest by two
+// __reduce_max_sync, the block's through a double-buffered pair of slots
+// per warp in shared memory: one barrier per round -- a warp cannot reach
+// round r + 2's write before every warp has passed round r + 1's barrier,
+// after its reads of round r), places the first vertex v1, and places the
+// second one v2 in the same round when v2 is not adjacent to v1: then v2's
+// key is unchanged by placing v1 while every other key can only fall, so v2
+// is exactly the next maximum-degree vertex (labels make keys distinct).  On
+// G(n, 0.3) about two vertices in three rounds go in pairs.  Finally the keys
+// of the placed vertices' remaining neighbours are decremented.
 template <int KP>
 __global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
                                                    uint32_t *__restrict__ order, int rows_in_smem)
 {
     extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *mx = sm;              // [2][8] warp maxima
-    uint32_t *srows = sm + 16;      // n * w words (optional)
+    uint32_t *mx = sm;              // [2 rounds][8 warps][2 keys]
+    uint32_t *srows = sm + 32;      // n * w words (optional)
     const uint32_t *R = rows;
     if (rows_in_smem) {
         for (uint32_t i = threadIdx.x; i < n * w; i += blockDim.x) srows[i] = rows[i];
@@ -156,31 +161,64 @@ __global__ void __launch_bounds__(256) order_kernel(uint32_t n, uint32_t w, cons
         }
         key[q] = k;
     }
-    for (uint32_t i = 0; i < n; ++i) {
-        uint32_t b = 0u;
+    uint32_t i = 0, rd = 0;
+    while (i < n) {
+        uint32_t a1 = 0u, a2 = 0u;  // this thread's two largest keys
 #pragma unroll
-        for (int q = 0; q < KP; ++q) b = key[q] > b ? key[q] : b;
-        b = __reduce_max_sync(FULLM, b);
-        volatile uint32_t *slot = mx + (i & 1u) * 8u;
-        if ((t & 31u) == 0u) slot[t >> 5] = b;
+        for (int q = 0; q < KP; ++q) {
+            const uint32_t k = key[q];
+            if (k > a1) {
+                a2 = a1;
+                a1 = k;
+            } else if (k > a2) {
+                a2 = k;
+            }
+        }
+        const uint32_t w1 = __reduce_max_sync(FULLM, a1);
+        const uint32_t w2 = __reduce_max_sync(FULLM, a1 == w1 ? a2 : a1);
+        volatile uint32_t *slot = mx + (rd & 1u) * 16u;
+        if ((t & 31u) == 0u) {
+            slot[2u * (t >> 5)] = w1;
+            slot[2u * (t >> 5) + 1u] = w2;
+        }
         __syncthreads();
-        uint32_t best = slot[0];
+        uint32_t b1 = 0u, b2 = 0u;
 #pragma unroll
-        for (int j = 1; j < 8; ++j) best = slot[j] > best ? slot[j] : best;
-        const uint32_t v = 4095u - (best & 4095u);
-        if (t == 0) order[i] = v;
-        const uint32_t *rv = R + (size_t)v * w;
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t x1 = slot[2 * j], x2 = slot[2 * j + 1];
+            if (x1 > b1) {
+                b2 = x2 > b1 ? x2 : b1;
+                b1 = x1;
+            } else if (x1 > b2) {
+                b2 = x1;
+            }
+        }
+        const uint32_t v1 = 4095u - (b1 & 4095u);
+        const uint32_t v2 = 4095u - (b2 & 4095u);
+        const uint32_t *r1 = R + (size_t)v1 * w;
+        const bool two = b2 != 0u && !((r1[v2 >> 5] >> (v2 & 31u)) & 1u);
+        const uint32_t *r2 = R + (size_t)v2 * w;
+        if (t == 0) {
+            order[i] = v1;
+            if (two) order[i + 1] = v2;
+        }
 #pragma unroll
         for (int q = 0; q < KP; ++q) {
             const uint32_t u = t + 256u * q;
             if (u < n) {
-                const uint32_t word = rv[u >> 5];
                 uint32_t k = key[q];
-                if (u == v) k = 0u;
-                else if (((word >> (u & 31u)) & 1u) && k) k -= 1u << 12;
+                if (u == v1 || (two && u == v2)) {
+                    k = 0u;
+                } else if (k) {
+                    uint32_t dec = (r1[u >> 5] >> (u & 31u)) & 1u;
+                    if (two) dec += (r2[u >> 5] >> (u & 31u)) & 1u;
+                    k -= dec << 12;
+                }
                 key[q] = k;
             }
         }
+        i += two ? 2u : 1u;
+        ++rd;
     }
 }
 
@@ -272,8 +310,8 @@ cudaError_t launch_order(uint32_t n, uint32_t w, const uint32_t *rows, uint32_t 
 {
     if (n == 0) return cudaSuccess;
     const size_t rbytes = (size_t)n * w * 4;
-    const int in_smem = (64 + rbytes) <= 200u * 1024u;
-    const size_t smem = 64 + (in_smem ? rbytes : 0);
+    const int in_smem = (128 + rbytes) <= 200u * 1024u;
+    const size_t smem = 128 + (in_smem ? rbytes : 0);
     const void *k = nullptr;
     void (*f)(uint32_t, uint32_t, const uint32_t *, uint32_t *, int) = nullptr;
     if (n <= 256) f = order_kernel<1>;
