@@ -68,8 +68,11 @@ __global__ void validate_kernel(uint32_t n, uint32_t w, const uint32_t *__restri
 // with the keys in registers: lane l owns the vertices of words
 // [l*JW, l*JW + JW), key = (degree + 1) << 12 | (4095 - u) while u is not
 // placed (0 once placed), so the maximum key is the highest remaining degree
-// with the smallest label.  A round takes the warp maximum, places that
-// vertex and decrements the keys of its remaining neighbours.
+// with the smallest label.  A round takes the warp's two largest keys,
+// places the first vertex and, when the second is not adjacent to it, the
+// second too (its key is then unchanged while every other key can only
+// fall, so it is the next pick), and decrements the keys of the placed
+// vertices' remaining neighbours.
 template <int JW>
 __device__ __forceinline__ void order_body(uint32_t n, uint32_t w, const uint32_t *__restrict__ rows,
                                            uint32_t *__restrict__ order, int rows_in_smem, uint32_t *sm)
@@ -100,26 +103,44 @@ __device__ __forceinline__ void order_body(uint32_t n, uint32_t w, const uint32_
             key[q * 32 + b] = u < n ? sdeg[u] : 0u;
         }
 
-    for (uint32_t i = 0; i < n; ++i) {
-        uint32_t best = 0;
+    for (uint32_t i = 0; i < n;) {
+        uint32_t a1 = 0u, a2 = 0u;
 #pragma unroll
-        for (int t = 0; t < 32 * JW; ++t) best = key[t] > best ? key[t] : best;
-        best = __reduce_max_sync(FULLM, best);
-        const uint32_t v = 4095u - (best & 4095u);
-        if (lane == 0) order[i] = v;
+        for (int t = 0; t < 32 * JW; ++t) {
+            const uint32_t k = key[t];
+            if (k > a1) {
+                a2 = a1;
+                a1 = k;
+            } else if (k > a2) {
+                a2 = k;
+            }
+        }
+        const uint32_t b1 = __reduce_max_sync(FULLM, a1);
+        const uint32_t b2 = __reduce_max_sync(FULLM, a1 == b1 ? a2 : a1);
+        const uint32_t v = 4095u - (b1 & 4095u);
+        const uint32_t v2 = 4095u - (b2 & 4095u);
         const uint32_t *rv = R + (size_t)v * w;
+        const bool two = b2 != 0u && !((rv[v2 >> 5] >> (v2 & 31u)) & 1u);
+        const uint32_t *rv2 = R + (size_t)v2 * w;
+        if (lane == 0) {
+            order[i] = v;
+            if (two) order[i + 1] = v2;
+        }
 #pragma unroll
         for (int q = 0; q < JW; ++q) {
             const uint32_t wi = lane * JW + q;
             const uint32_t word = wi < w ? rv[wi] : 0u;
+            const uint32_t word2 = (two && wi < w) ? rv2[wi] : 0u;
 #pragma unroll
             for (int b = 0; b < 32; ++b) {
                 uint32_t k = key[q * 32 + b];
-                if (wi * 32u + b == v) k = 0u;
-                else if (((word >> b) & 1u) && k) k -= 1u << 12;
+                const uint32_t u = wi * 32u + b;
+                if (u == v || (two && u == v2)) k = 0u;
+                else if (k) k -= (((word >> b) & 1u) + ((word2 >> b) & 1u)) << 12;
                 key[q * 32 + b] = k;
             }
         }
+        i += two ? 2u : 1u;
     }
 }
 
