@@ -425,9 +425,12 @@ int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
                         const mce_options *opts, mce_result *res);
 
 /* Served form: requests are admitted by device memory and run with the
- * others already on the GPU; mce_poll never blocks.  Each admitted request
- * runs its whole path on one of 128 streams with a grid sized by its expected
- * cost; requests overlap on the device only as far as CUDA maps their streams
+ * others already on the GPU; mce_poll never blocks.  While four or more
+ * requests with default options wait, up to 256 of them (each expecting at
+ * most 10^6 maximal cliques) run as one batched launch; otherwise an
+ * admitted request runs its whole path on one of 128 streams with a grid of
+ * one block per 20,000 expected maximal cliques (at most four per SM);
+ * requests overlap on the device only as far as CUDA maps their streams
  * to separate hardware queues (CUDA_DEVICE_MAX_CONNECTIONS, read when a
  * context is created).  Loading the library sets it to 32 unless the process
  * set it already, so a process that loads the library before it creates its

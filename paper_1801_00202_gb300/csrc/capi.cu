@@ -256,8 +256,12 @@ Tuning mce::default_tuning()
         // iterations of a busy warp: with fetch-and-add ring tickets the
         // checks are cheap enough that checking more often than every 16 /
         // 64 iterations paid (G(1000, 0.3): 7.8 -> 7.4 ms; G(700, 0.3): 2.2
-        // -> 1.7 ms)
-        Tuning d{0u, 0u, 8u, 16u, 2000u, 50000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 4u};  // 0: thresholds by density
+        // -> 1.7 ms).  Served form: a request alone gets a block per 20,000
+        // expected maximal cliques, and requests expecting up to 10^6 share
+        // micro-batches (on the served workload, 10,400 -> 11,300 requests/s
+        // closed loop and p99 6.3 -> 3.9 ms at 0.7x that load, against one
+        // block per 50,000 and micro-batches up to 10^5)
+        Tuning d{0u, 0u, 8u, 16u, 2000u, 20000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 4u, 1000u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -281,6 +285,7 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "serve_t2")) d.serve_t2 = val;
                 else if (!std::strcmp(key, "batch_wide")) d.batch_wide = val;
                 else if (!std::strcmp(key, "batch_split")) d.batch_split = val;
+                else if (!std::strcmp(key, "serve_bcost")) d.serve_bcost = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -1992,10 +1997,9 @@ namespace {
 constexpr int kServeSlots = 128;
 constexpr size_t kServeStackBytes = 56 * 1024;  // shared-memory stack per block
 // Micro-batches: while at least kBatchMin requests that can share a launch
-// wait, up to kBatchMax of them (each expecting at most kBatchCost maximal
-// cliques) run as one batched launch on one stream slot.
+// wait, up to kBatchMax of them (each expecting at most serve_bcost
+// thousand maximal cliques) run as one batched launch on one stream slot.
 constexpr size_t kBatchMin = 4, kBatchMax = 256;
-constexpr double kBatchCost = 1e5;
 
 struct MicroBatch;
 
@@ -2321,7 +2325,7 @@ extern "C" int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, m
     // default launch options and a small expected cost: may share a launch
     const bool batchable = !o.lanes_per_subtree && !o.words_per_lane && !o.threads_per_block && !o.blocks &&
                            !o.split_min_p && !o.stack_levels && !o.queue_log2 && !o.flags && !o.timeout_ns &&
-                           cost <= kBatchCost;
+                           cost <= 1e3 * default_tuning().serve_bcost;
     if (!o.threads_per_block) o.threads_per_block = 256;
     if (!o.blocks) {
         const double per_block = default_tuning().serve_cpb;

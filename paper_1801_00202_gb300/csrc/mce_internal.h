@@ -100,6 +100,7 @@ struct Tuning {
     uint32_t serve_t2;      // served requests use the lane tier too (its region beside the capped stack)
     uint32_t batch_wide;    // batched form by default: 512 threads, at most two words per lane (1), or the plain shapes (0)
     uint32_t batch_split;   // batched form: parts of about 1/(blocks * batch_split) of a bucket's cost (0: no split)
+    uint32_t serve_bcost;   // served form: largest expected maximal cliques (thousands) of a micro-batched request
 };
 
 // The lane tier (second search tier): a frame whose P u X has at most 32
