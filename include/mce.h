@@ -65,6 +65,8 @@ extern "C" {
 #define MCE_ETIMEOUT  -5   /* a bounded wait (device or host) gave up        */
 #define MCE_EOVERFLOW -6   /* the device work queue overflowed               */
 #define MCE_ENOTIMPL  -7   /* option combination not implemented             */
+#define MCE_ECANCELED -8   /* the request was cancelled before it ran        */
+#define MCE_EBUSY     -9   /* the request already runs (or ran): not cancelled */
 
 #define MCE_NMAX 4096u     /* largest number of vertices on the bitset path  */
 #define MCE_NMAX_SPARSE 65535u  /* largest graph mce_load_edges accepts:
@@ -439,8 +441,33 @@ int mce_enumerate_batch(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count,
 int mce_submit(mce_ctx *ctx, mce_graph *g, const mce_options *opts, mce_ticket *out);
 int mce_poll(mce_ctx *ctx, mce_ticket t, mce_result *res);
 int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_result *res);
+/* Cancel a request that is still queued: it will not run, and mce_poll /
+ * mce_wait deliver it with status MCE_ECANCELED.  MCE_EBUSY when it already
+ * runs or has finished (it completes normally), MCE_EINVAL for an unknown
+ * ticket. */
+int mce_cancel(mce_ctx *ctx, mce_ticket t);
 
 const char *mce_strerror(int code);
+
+/* Host-side fault injection, for failure-detection tests (nothing on the GPU
+ * is made to fail).  Arms `site` so that, after `skip` more passes through
+ * it, the next `count` passes fail as the real failure would:
+ *   MCE_FAULT_ALLOC  a device allocation of the library fails (MCE_ENOMEM;
+ *                    whatever the call allocated so far is released);
+ *   MCE_FAULT_COPY   a host-to-device copy of an input graph fails
+ *                    (MCE_ECUDA from mce_load_edges / mce_load_bitset);
+ *   MCE_FAULT_ADMIT  the served form's admission finds no memory for a
+ *                    request, which stays queued and is tried again.
+ * count 0 disarms the site.  Process-wide; the environment variable
+ * MCE_FAULT="site:skip:count" (site = alloc, copy or admit) arms one site
+ * when the library is loaded.  Returns MCE_EINVAL for an unknown site. */
+#define MCE_FAULT_ALLOC 1
+#define MCE_FAULT_COPY  2
+#define MCE_FAULT_ADMIT 3
+int mce_fault_inject(int site, uint32_t skip, uint32_t count);
+/* Device memory (bytes) the context's library allocations hold now:
+ * graphs, batches, request scratch (0 once everything is released). */
+uint64_t mce_ctx_mem_used(const mce_ctx *ctx);
 
 /* ----------------------------------------------------------------------- */
 /* Diagnostics                                                               */

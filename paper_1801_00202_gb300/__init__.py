@@ -26,6 +26,8 @@ from .build import LIB as _LIB_PATH, build  # noqa: F401
 MCE_OK, MCE_PENDING = 0, 1
 MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETRUNC = -1, -2, -3, -4
 MCE_ETIMEOUT, MCE_EOVERFLOW, MCE_ENOTIMPL = -5, -6, -7
+MCE_ECANCELED, MCE_EBUSY = -8, -9
+MCE_FAULT_ALLOC, MCE_FAULT_COPY, MCE_FAULT_ADMIT = 1, 2, 3
 MCE_NMAX, MCE_NMAX_SPARSE = 4096, 65535
 
 MCE_PIVOT_GREEDY, MCE_PIVOT_GREEDY_TX, MCE_PIVOT_TOMITA, MCE_PIVOT_GREEDY_NX = 0, 1, 2, 3
@@ -124,6 +126,9 @@ _SIGS = {
     "mce_submit": (C.c_int, [_VP, _VP, C.POINTER(Options), C.POINTER(_U64)]),
     "mce_poll": (C.c_int, [_VP, _U64, C.POINTER(Result)]),
     "mce_wait": (C.c_int, [_VP, _U64, _U64, C.POINTER(Result)]),
+    "mce_cancel": (C.c_int, [_VP, _U64]),
+    "mce_fault_inject": (C.c_int, [C.c_int, _U32, _U32]),
+    "mce_ctx_mem_used": (_U64, [_VP]),
     "mce_strerror": (C.c_char_p, [C.c_int]),
     "mce_trace_enable": (C.c_int, [_VP, _U64]),
     "mce_measure_peaks": (C.c_int, [C.c_int, C.POINTER(Peaks)]),
@@ -184,6 +189,12 @@ def _check(rc: int, what: str) -> int:
 
 def mce_strerror(code: int) -> str:
     return lib().mce_strerror(code).decode()
+
+
+def mce_fault_inject(site: int, skip: int = 0, count: int = 1) -> int:
+    """Arm a host-side fault site (MCE_FAULT_ALLOC / COPY / ADMIT): after
+    `skip` passes, the next `count` fail; count 0 disarms."""
+    return int(lib().mce_fault_inject(site, skip, count))
 
 
 def mce_measure_peaks(device: int = 0) -> dict:
@@ -329,6 +340,15 @@ class Context:
         if res is None:
             raise MceError(rc, "mce_wait")
         return res
+
+    def cancel(self, ticket: int) -> int:
+        """mce_cancel: MCE_OK when the queued request will not run (its
+        result then carries MCE_ECANCELED), MCE_EBUSY when it already runs."""
+        return int(lib().mce_cancel(self.handle, ticket))
+
+    def mem_used(self) -> int:
+        """mce_ctx_mem_used: device bytes the context's allocations hold."""
+        return int(lib().mce_ctx_mem_used(self.handle))
 
     def load_bitset(self, n: int, rows) -> "Graph":
         rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32))

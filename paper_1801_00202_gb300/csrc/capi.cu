@@ -28,6 +28,55 @@ namespace {
 // before it creates its CUDA context gets 32 unless it chose a value itself.
 __attribute__((constructor)) void default_connections() { setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0); }
 
+// Host-side fault injection (mce_fault_inject): per site, passes to let
+// through and failures to make.  `armed` keeps the unarmed path to one
+// relaxed load.
+struct FaultSite {
+    std::mutex mu;
+    uint32_t skip = 0, count = 0;
+};
+FaultSite g_fault[4];
+std::atomic<uint32_t> g_fault_armed{0};
+
+bool fault_fires(int site)
+{
+    if (g_fault_armed.load(std::memory_order_relaxed) == 0u) return false;
+    FaultSite &f = g_fault[site];
+    std::lock_guard<std::mutex> lk(f.mu);
+    if (f.count == 0u) return false;
+    if (f.skip) {
+        --f.skip;
+        return false;
+    }
+    if (--f.count == 0u) g_fault_armed.fetch_sub(1u);
+    return true;
+}
+
+int fault_arm(int site, uint32_t skip, uint32_t count)
+{
+    if (site < MCE_FAULT_ALLOC || site > MCE_FAULT_ADMIT) return MCE_EINVAL;
+    FaultSite &f = g_fault[site];
+    std::lock_guard<std::mutex> lk(f.mu);
+    if (f.count) g_fault_armed.fetch_sub(1u);
+    f.skip = skip;
+    f.count = count;
+    if (count) g_fault_armed.fetch_add(1u);
+    return MCE_OK;
+}
+
+__attribute__((constructor)) void fault_from_env()
+{
+    const char *env = std::getenv("MCE_FAULT");
+    if (!env) return;
+    char site[16] = {0};
+    unsigned skip = 0, count = 0;
+    if (std::sscanf(env, "%15[a-z]:%u:%u", site, &skip, &count) != 3) return;
+    const int s = !std::strcmp(site, "alloc") ? MCE_FAULT_ALLOC
+                  : !std::strcmp(site, "copy") ? MCE_FAULT_COPY
+                  : !std::strcmp(site, "admit") ? MCE_FAULT_ADMIT : 0;
+    if (s) fault_arm(s, skip, count);
+}
+
 // ---------------------------------------------------------------------------
 // Launch configuration
 
@@ -536,6 +585,8 @@ struct DevicePick {
 
 int dalloc(mce_ctx *ctx, void **p, size_t bytes, cudaStream_t s = nullptr)
 {
+    *p = nullptr;
+    if (fault_fires(MCE_FAULT_ALLOC)) return MCE_ENOMEM;
     if (bytes == 0) bytes = 256;
     if (ctx->budget && ctx->used.fetch_add(bytes) + bytes > ctx->budget) {
         ctx->used.fetch_sub(bytes);
@@ -673,7 +724,9 @@ int load_edges_csr(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint64_t m, mce
         g->d_adj = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(g->d_off) +
                                                 round_up(((uint64_t)n + 1) * 4, 256));
         e = cudaMemsetAsync(d_status, 0, 64, ctx->stream);
-        if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_uv, uv, m * 8, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess && m)
+            e = fault_fires(MCE_FAULT_COPY) ? cudaErrorInvalidValue
+                                            : cudaMemcpyAsync(d_uv, uv, m * 8, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = outer_csr_from_edges(n, m, d_uv, temp, tb, g->d_off, g->d_adj, d_status, ctx->stream);
         if (e != cudaSuccess) rc = MCE_ECUDA;
     }
@@ -720,7 +773,9 @@ extern "C" int mce_load_edges(mce_ctx *ctx, uint32_t n, const uint32_t *uv, uint
     cudaError_t e = cudaSuccess;
     if (rc == MCE_OK) {
         e = cudaMemsetAsync(d_status, 0, 64, ctx->stream);
-        if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_uv, uv, m * 8, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess && m)
+            e = fault_fires(MCE_FAULT_COPY) ? cudaErrorInvalidValue
+                                            : cudaMemcpyAsync(d_uv, uv, m * 8, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = launch_edges_to_rows(n, m, d_uv, g->w, g->d_rows, d_status, ctx->stream);
         if (e != cudaSuccess) rc = MCE_ECUDA;
     }
@@ -756,7 +811,9 @@ extern "C" int mce_load_bitset(mce_ctx *ctx, uint32_t n, const uint32_t *rows, u
     if (rc == MCE_OK) {
         e = cudaMemsetAsync(d_status, 0, 64, ctx->stream);
         if (e == cudaSuccess && n)
-            e = cudaMemcpyAsync(g->d_rows, rows, (size_t)n * words_per_row * 4, cudaMemcpyHostToDevice, ctx->stream);
+            e = fault_fires(MCE_FAULT_COPY)
+                    ? cudaErrorInvalidValue
+                    : cudaMemcpyAsync(g->d_rows, rows, (size_t)n * words_per_row * 4, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = launch_validate_rows(n, g->w, g->d_rows, d_status, ctx->stream);
         if (e != cudaSuccess) rc = MCE_ECUDA;
     }
@@ -2072,6 +2129,7 @@ void retire(Server *sv, Request *r, int rc)
 // Launch one request on a free slot; false when it must wait.
 bool admit(Server *sv, Request *r)
 {
+    if (fault_fires(MCE_FAULT_ADMIT)) return false;  // as if out of memory: stays queued
     int slot = -1;
     for (int i = 0; i < kServeSlots; ++i)
         if (!sv->busy[i]) { slot = i; break; }
@@ -2398,6 +2456,31 @@ extern "C" int mce_wait(mce_ctx *ctx, mce_ticket t, uint64_t timeout_ns, mce_res
     return deliver(sv, r, res);
 }
 
+extern "C" int mce_cancel(mce_ctx *ctx, mce_ticket t)
+{
+    if (!ctx || !ctx->server) return MCE_EINVAL;
+    Server *sv = ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->all.find(t);
+        if (it == sv->all.end()) return MCE_EINVAL;
+        Request *r = it->second;
+        if (r->state != 0) return MCE_EBUSY;
+        auto q = std::find(sv->pending.begin(), sv->pending.end(), r);
+        if (q == sv->pending.end()) return MCE_EBUSY;
+        sv->pending.erase(q);
+        r->rc = MCE_ECANCELED;
+        r->state = 2;
+        r->t_done = std::chrono::steady_clock::now();
+    }
+    sv->done_cv.notify_all();
+    return MCE_OK;
+}
+
+extern "C" int mce_fault_inject(int site, uint32_t skip, uint32_t count) { return fault_arm(site, skip, count); }
+
+extern "C" uint64_t mce_ctx_mem_used(const mce_ctx *ctx) { return ctx ? ctx->used.load() : 0ull; }
+
 extern "C" int mce_trace_enable(void *d_buf, uint64_t bytes)
 {
     g_trace = bytes >= 16 ? d_buf : nullptr;
@@ -2417,6 +2500,8 @@ extern "C" const char *mce_strerror(int code)
     case MCE_ETIMEOUT: return "timed out";
     case MCE_EOVERFLOW: return "work queue overflow";
     case MCE_ENOTIMPL: return "not implemented";
+    case MCE_ECANCELED: return "cancelled";
+    case MCE_EBUSY: return "already running";
     default: return "unknown error";
     }
 }

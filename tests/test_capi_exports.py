@@ -63,3 +63,14 @@ def test_loading_the_library_asks_for_32_hardware_queues():
     env["CUDA_DEVICE_MAX_CONNECTIONS"] = "4"
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
     assert r.stdout.strip() == "4"
+
+
+def test_fault_sites_arm_and_disarm(lib):
+    import paper_1801_00202_gb300 as m
+    assert m.mce_fault_inject(0, 0, 1) == m.MCE_EINVAL
+    assert m.mce_fault_inject(4, 0, 1) == m.MCE_EINVAL
+    for site in (m.MCE_FAULT_ALLOC, m.MCE_FAULT_COPY, m.MCE_FAULT_ADMIT):
+        assert m.mce_fault_inject(site, 3, 2) == m.MCE_OK
+        assert m.mce_fault_inject(site, 0, 0) == m.MCE_OK
+    assert m.mce_strerror(m.MCE_ECANCELED) == "cancelled"
+    assert m.mce_strerror(m.MCE_EBUSY) == "already running"
