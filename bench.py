@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -106,6 +107,9 @@ BASELINE_SAMPLE_NODES = 5_000_000   # cpu_baseline leg (about 10-30 s)
 # [0.1, 0.9], same cap, arrivals at SERVE_LOAD x the capacity measured on the
 # warm-up requests (saturating), then a second pass at LATENCY_LOAD x capacity.
 BATCH_GRAPHS = 4096
+# The literal (uncapped) batched distribution, attempted on a few graphs with a
+# short budget and reported as did-not-finish.
+LITERAL_SAMPLE, LITERAL_TIMEOUT_NS = 32, 20_000_000
 SERVE_LOAD, LATENCY_LOAD = 1.2, 0.7
 # DRAM bytes (read + write) of one search-kernel launch, from a one-pass ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel built
@@ -284,6 +288,11 @@ def _gen_batch(i: int):
     return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
 
 
+def _gen_literal(i: int):
+    g = synth.batch_graph(i, cap=math.inf)   # the literal distribution: first draw kept
+    return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
+
+
 def _gen_served(r: int):
     g = synth.served_graph(r)
     return g.n, g.p, g.draws, synth.to_bitset(g.n, g.uv)
@@ -309,6 +318,7 @@ def generate_forms(args):
     with mp.get_context("spawn").Pool(cores) as pool:
         batch = pool.map(_gen_batch, range(args.batch_graphs), chunksize=32)
         served = pool.map(_gen_served, range(total), chunksize=64)
+        literal = pool.map(_gen_literal, range(LITERAL_SAMPLE), chunksize=4)
         gen_s = time.perf_counter() - t
         base = None
         if args.oracle_sample and not args.no_cpu_baseline:
@@ -325,7 +335,7 @@ def generate_forms(args):
                     "sample": f"Bron-Kerbosch with the Tomita pivot, one graph per host core, on every "
                               f"{step}th graph of the batched workload ({len(sample)} graphs, "
                               f"{cliques} maximal cliques, {wall:.1f} s)"}
-    return batch, served, {"cores": cores, "seconds": gen_s}, base
+    return batch, served, {"cores": cores, "seconds": gen_s}, base, literal
 
 
 def _work(results, ns):
@@ -438,6 +448,34 @@ def _open_loop(ctx, graphs, arrivals, opts):
         pend = keep
     finish = max(a + l for a, l in zip(arrivals, lat))
     return res, lat, finish - arrivals[0]
+
+
+def literal_form(mce, ctx, specs, cliques_per_s):
+    """The first LITERAL_SAMPLE graphs of the batched workload as written, with
+    no cap on E[maximal cliques]: one batch with a short per-graph budget
+    (MCE_ETIMEOUT after 10 x LITERAL_TIMEOUT_NS of search), reported as did
+    not finish where the budget ran out, with the time the expected clique
+    counts project at the capped workload's measured rate."""
+    graphs = [ctx.load_bitset(n, rows) for n, _, _, rows in specs]
+    t = time.perf_counter()
+    b = mce.Batch(ctx, graphs, mce.options(timeout_ns=LITERAL_TIMEOUT_NS))
+    res = b.run(raise_on_error=False)
+    wall = time.perf_counter() - t
+    b.close()
+    for g in graphs:
+        g.free()
+    emu = [synth.expected_maximal_cliques(n, p) for n, p, _, _ in specs]
+    done = [r["status"] == 0 for r in res]
+    dnf = [r["status"] == mce.MCE_ETIMEOUT for r in res]
+    left = sum(e for e, d in zip(emu, done) if not d)
+    return {"graphs": len(specs), "finished": sum(done), "did_not_finish": sum(dnf),
+            "other_status": len(specs) - sum(done) - sum(dnf), "budget_s_per_graph": 10 * LITERAL_TIMEOUT_NS / 1e9,
+            "wall_s": wall, "cliques_finished": sum(r["count"] for r, d in zip(res, done) if d),
+            "expected_cliques_unfinished": left, "largest_expected": max(emu),
+            "projected_hours_at_capped_rate": left / cliques_per_s / 3600.0,
+            "note": "n uniform [32,512], p uniform [0.2,0.8] with no cap on E[maximal cliques] "
+                    "(the capped workload redraws (n,p) while E > 1e6); first draws of graphs 0.."
+                    f"{len(specs) - 1}"}
 
 
 def served_form(mce, torch, ctx, specs, opts, args):
@@ -872,13 +910,15 @@ def run_ours(args):
 
     forms = None
     if forms_in is not None:
-        batch_specs, served_specs, gen, batch_base = forms_in
+        batch_specs, served_specs, gen, batch_base, literal_specs = forms_in
         fctx = mce.Context(local, stream=s)
         fclk = ClockSampler(local)
         fclk.start()
         forms = {"batched": batched_form(mce, torch, fctx, s, batch_specs, mce.options(), args, flush_l2)}
         forms["batched"]["cpu_oracle_all_cores"] = batch_base
         forms["served"] = served_form(mce, torch, fctx, served_specs, mce.options(), args)
+        forms["literal_batched_sample"] = literal_form(mce, fctx, literal_specs,
+                                                       forms["batched"]["batched"]["cliques_per_s"])
         forms["clocks"] = fclk.stop()
         forms["generation"] = gen
         fctx.close()
