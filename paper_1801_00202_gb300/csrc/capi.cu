@@ -151,19 +151,29 @@ void plan_stack_for(uint32_t base, int G, int K, unsigned threads, size_t limit,
     total = offset + (size_t)levels * per_level;
 }
 
-// Default subtree shape: up to four words per lane, so that several
-// subtrees share every warp instruction (the search is issue-bound), one
-// thread per subtree up to 64 vertices.
+// Default subtree shape (lanes G x words per lane K).  With the lane tier
+// taking the small subproblems, one word per lane and as many lanes as the
+// row has words won up to 24 words per row: measured on one graph of each
+// size, whole path (old four-word shapes in brackets), G(45) Moon-Moser 1.33
+// (1.48) ms, G(100, 0.5) 0.27 (0.29), G(128, 0.7) 1.29 (1.84), G(200, 0.55)
+// 1.36 (2.10), G(256, 0.5) 1.44 (2.52), G(300, 0.5) 2.11 (2.96), G(700, 0.3)
+// 1.55 (1.66) ms.  At 13-16 words two words per lane led (G(500, 0.4): 2.63
+// against 2.76 with one and 3.15 with four), at 25-32 four (G(1000, 0.3):
+// 7.28 against 7.96 with two and 8.97 with one: 32 one-word lanes per
+// subtree leave a block too few subtrees), above 32 two (G(1500, 0.15) and
+// G(2000, 0.1): 2.53 / 2.60 against 2.59 / 2.67 with four).
 void default_shape(uint32_t n, int &G, int &K)
 {
     const uint32_t W = std::max<uint32_t>(1, (n + 31) / 32);
     if (W <= 1) { G = 1; K = 1; }
-    else if (W <= 2) { G = 1; K = 2; }
-    else if (W <= 4) { G = 2; K = 2; }
-    else if (W <= 8) { G = 2; K = 4; }
-    else if (W <= 16) { G = 4; K = 4; }
+    else if (W <= 2) { G = 2; K = 1; }
+    else if (W <= 4) { G = 4; K = 1; }
+    else if (W <= 8) { G = 8; K = 1; }
+    else if (W <= 12) { G = 16; K = 1; }
+    else if (W <= 16) { G = 8; K = 2; }
+    else if (W <= 24) { G = 32; K = 1; }
     else if (W <= 32) { G = 8; K = 4; }
-    else if (W <= 64) { G = 16; K = 4; }
+    else if (W <= 64) { G = 32; K = 2; }
     else { G = 32; K = 4; }
 }
 

@@ -29,8 +29,8 @@ def mce():
 CASES = [
     # Moon-Moser on 36 vertices: 3^12 cliques; every level keeps all but three
     # vertices, so a split threshold of 9 publishes the top nine levels
-    ("mm36", 36, synth.moon_moser(12), "greedy", dict(blocks=2, threads=64, split_min_p=9)),
-    ("mm36_tx", 36, synth.moon_moser(12), "tx", dict(blocks=2, threads=64, split_min_p=9)),
+    ("mm36", 36, synth.moon_moser(12), "greedy", dict(blocks=2, threads=64, lanes=1, words=2, split_min_p=9)),
+    ("mm36_tx", 36, synth.moon_moser(12), "tx", dict(blocks=2, threads=64, lanes=1, words=2, split_min_p=9)),
     ("gnp150", 150, synth.gnp(150, 0.5, 930), "greedy", dict(blocks=3, threads=96, split_min_p=10)),
     ("gnp150_tomita", 150, synth.gnp(150, 0.5, 930), "tomita", dict(blocks=3, threads=96, split_min_p=10)),
     ("gnp400", 400, synth.gnp(400, 0.3, 931), "greedy", dict(blocks=2, threads=128, split_min_p=12)),
