@@ -262,7 +262,7 @@ int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_r
  *    (mce_scratch_bytes(n, opts) > MCE_STATIC_SCRATCH_BYTES).  The default
  *    work queue grows with the number of resident subtree groups, so the
  *    bound depends on the GPU: on a 152-SM GB300 the default options fit for
- *    every n <= MCE_NMAX (at most about 27 MiB, for n <= 32). */
+ *    every n <= MCE_NMAX (at most about 26 MiB, for n <= 32). */
 #define MCE_STATIC_SCRATCH_BYTES (32u << 20)
 int mce_enumerate_device_static(uint32_t n, uint32_t words_per_row, const uint32_t *d_rows,
                                 const mce_options *opts, uint64_t *d_out, void *stream);

@@ -233,17 +233,38 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     // gets fewer warps so that they fit, or they are read from L2.
     const Tuning tu = default_tuning();
     const bool t2 = !c.list && G >= 2 && tu.t2_p != 0 && (stack_cap == ~(size_t)0 || tu.serve_t2);
-    const size_t t2w = t2 ? t2_warp_bytes(tu.t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY) : 0;
+    uint32_t t2_levels = tu.t2_levels;
+    size_t t2w = t2 ? t2_warp_bytes(t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY) : 0;
     auto fits = [&](bool rows_smem, unsigned threads) {
         return round_up(search_smem(n, c.wp, rows_smem, c.list), 16) + (size_t)(threads / 32) * t2w <= limit;
     };
     c.smem = c.wp <= 32 && fits(true, c.threads);
     if (!c.smem && t2 && tu.t2_smem_rows && c.wp <= 32 && !o.threads_per_block) {
-        for (unsigned th = c.threads - 64; th >= 128 && !c.smem; th -= 64)
-            if (fits(true, th)) {
-                c.threads = th;
-                c.smem = true;
+        // rows in shared memory with as many warps as fit beside them (one
+        // warp at a time), with fewer lane-tier stack levels in shared memory
+        // when that buys warps (deeper levels go to local memory);
+        // G(1000, 0.3): 8 warps with four levels, 9 with three, 10 with two
+        auto most = [&]() {
+            unsigned th = c.threads;
+            while (th >= 128 && !fits(true, th)) th -= 32;
+            return th >= 128 ? th : 0u;
+        };
+        unsigned best = 0;
+        uint32_t best_levels = t2_levels;
+        for (uint32_t lv = t2_levels; lv >= 1; --lv) {
+            t2w = t2_warp_bytes(lv, o.pivot_mode != MCE_PIVOT_GREEDY);
+            const unsigned th = most();
+            if (th > best) {
+                best = th;
+                best_levels = lv;
             }
+        }
+        t2_levels = best_levels;
+        t2w = t2_warp_bytes(t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY);
+        if (best) {
+            c.threads = best;
+            c.smem = true;
+        }
     }
     if (t2 && !fits(c.smem, c.threads) && !o.threads_per_block)
         while (c.threads > 128 && !fits(c.smem, c.threads)) c.threads -= 64;
@@ -254,7 +275,7 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     size_t base = search_smem(n, c.wp, c.smem, c.list);
     if (t2_on) {
         c.t2_offset = (uint32_t)round_up(base, 16);
-        c.t2_levels = tu.t2_levels;
+        c.t2_levels = t2_levels;
         c.t2_max_p = tu.t2_p;
         base = c.t2_offset + (size_t)(c.threads / 32) * t2w;
     }

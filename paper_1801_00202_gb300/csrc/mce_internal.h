@@ -357,7 +357,7 @@ __host__ __device__ inline size_t smem_rows_bytes(uint32_t n, uint32_t wp, bool 
 }
 __host__ __device__ inline size_t smem_local_offset(uint32_t n, uint32_t wp, bool rows_in_smem)
 {
-    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 + ((size_t)n + 1) * 8 +
+    return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 +
            (((size_t)n + 1) * 4 + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false)

@@ -917,7 +917,7 @@ struct T2Warp {
 // 32-bit sets).  Divergent by design: no warp collectives inside.
 template <int PIVOT>
 __device__ __forceinline__ void t2_step(T2Lane &t, const T2Warp &m, unsigned lane, const uint64_t *hv,
-                                        const uint64_t *hk, uint32_t *hist, uint64_t *out, uint32_t pivot_mode,
+                                        uint32_t *hist, uint64_t *out, uint32_t pivot_mode,
                                         uint32_t (&spill)[32][kT2Fields], Counters &cn, unsigned *busy_lanes)
 {
     if (!t.busy) return;
@@ -933,7 +933,7 @@ __device__ __forceinline__ void t2_step(T2Lane &t, const T2Warp &m, unsigned lan
     if (Pc == 0u) {
         if (Xc == 0u) {  // P u X empty: R u {v} is a maximal clique
             ++cn.cnt;
-            cn.hash += mix64(Sc ^ hk[k]);
+            cn.hash += mix64(Sc ^ mix64((uint64_t)k));
             cn.max = k > cn.max ? k : cn.max;
             const unsigned old = atomicAdd(&hist[k], 1u);
             if (old == 0xffffffffu)
@@ -1023,7 +1023,7 @@ __device__ __forceinline__ void t2_step(T2Lane &t, const T2Warp &m, unsigned lan
 // Called by all 32 lanes of every warp.
 template <int G, int K, bool SMEM, int PIVOT, bool LIST>
 __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint32_t *rows, const uint64_t *hv,
-                                            const uint64_t *hk, uint32_t *hist, const LocalQ &lq, const Thresholds th,
+                                            uint32_t *hist, const LocalQ &lq, const Thresholds th,
                                             uint32_t *stack_smem, int stack_smem_levels, unsigned char *t2_smem,
                                             Counters &cn)
 {
@@ -1344,7 +1344,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (t2any) {
                 const unsigned g1 = __ballot_sync(FULL, work);
                 if (32u - (unsigned)__popc(busym) < GPW || (g1 == 0u && (++t2it & 3u) != 0u)) {
-                    t2_step<PIVOT>(t2, t2m, g.lane, hv, hk, hist, prm.out, prm.pivot_mode, t2_spill, cn,
+                    t2_step<PIVOT>(t2, t2m, g.lane, hv, hist, prm.out, prm.pivot_mode, t2_spill, cn,
                                    &lq.h->t2_busy);
                     continue;
                 }
@@ -1686,7 +1686,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
         if (lead && !bp && !bx) {  // P u X empty: R u {v} is a maximal clique
             const unsigned k = rs + 1u;
             ++cn.cnt;
-            cn.hash += mix64(Sc ^ hk[k]);
+            cn.hash += mix64(Sc ^ mix64((uint64_t)k));
             cn.max = k > cn.max ? k : cn.max;
             const unsigned old = atomicAdd(&hist[k], 1u);
             if (old == 0xffffffffu)
@@ -1900,8 +1900,7 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
     const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
     uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
     uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
-    uint64_t *hk = hv + n;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(hk + n + 1);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
     const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
     local_queue_reset(lq, (blockDim.x / 32u) * (32u / G));
 
@@ -1911,7 +1910,6 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) hv[i] = mix64((uint64_t)prm.order[i] + 1u);
-    for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hk[i] = mix64((uint64_t)i);
     for (uint32_t i = threadIdx.x; i <= n; i += blockDim.x) hist[i] = 0u;
     bool staged = true;
     if (SMEM) staged = stage_rows(srows, prm.rows, (uint32_t)rbytes, (uint32_t)__cvta_generic_to_shared(&mbar), 0u);
@@ -1925,7 +1923,7 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
     Counters cn;
     cn.diag = lq.h->diag;
     if (ok)
-        search_loop<G, K, SMEM, PIVOT, LIST>(prm, SMEM ? srows : prm.rows, hv, hk, hist, lq, th, stack_smem,
+        search_loop<G, K, SMEM, PIVOT, LIST>(prm, SMEM ? srows : prm.rows, hv, hist, lq, th, stack_smem,
                                        (int)prm.stack_smem_levels, smem_raw + prm.t2_offset, cn);
     flush_counters(cn, prm.out);
     __syncthreads();
@@ -1974,8 +1972,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         const size_t rbytes = smem_rows_bytes(n, WP, SMEM);
         uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
         uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
-        uint64_t *hk = hv + n;
-        uint32_t *hist = reinterpret_cast<uint32_t *>(hk + n + 1);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
         const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
         local_queue_reset(lq, bp.groups_per_block);
         const bool valid = gd.out[MCE_OUT_STATUS] == 0ull;
@@ -2025,7 +2022,6 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         }
         for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
             hv[j] = mix64((uint64_t)(sub ? gd.label[gd.order[j]] : gd.order[j]) + 1u);
-        for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hk[j] = mix64((uint64_t)j);
         for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) hist[j] = 0u;
 
         // ChoosePivotOrdered at the root: the key (score + 1) << 12 | (4095 -
@@ -2176,7 +2172,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         Counters cn;
         cn.diag = lq.h->diag;
         if (ok)
-            search_loop<G, K, SMEM, PIVOT, false>(prm, SMEM ? srows : gd.ren, hv, hk, hist, lq, th,
+            search_loop<G, K, SMEM, PIVOT, false>(prm, SMEM ? srows : gd.ren, hv, hist, lq, th,
                                            reinterpret_cast<uint32_t *>(smem_raw + bp.stack_offset),
                                            (int)bp.stack_smem_levels, smem_raw + bp.t2_offset, cn);
         flush_counters(cn, gd.out);
