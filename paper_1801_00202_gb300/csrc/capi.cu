@@ -93,6 +93,7 @@ struct Config {
     bool list = false;  // frames carry R (clique listing)
     uint32_t t2_offset = 0, t2_levels = 0, t2_max_p = 0;  // lane tier (t2_max_p 0: off)
     bool seed = false;  // start from the root's children
+    uint32_t local_slots = kLocalSlots;  // block ring slots
     SearchImpl impl{nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -132,9 +133,9 @@ uint32_t next_pow2(uint64_t x)
     return (uint32_t)p;
 }
 
-size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false)
+size_t search_smem(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false, uint32_t slots = kLocalSlots)
 {
-    return search_smem_bytes(n, wp, rows_in_smem, list);
+    return search_smem_bytes(n, wp, rows_in_smem, list, slots);
 }
 
 constexpr uint32_t kListFlags = MCE_LIST | MCE_LIST_SORTED;
@@ -236,29 +237,37 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
     uint32_t t2_levels = tu.t2_levels;
     size_t t2w = t2 ? t2_warp_bytes(t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY) : 0;
     auto fits = [&](bool rows_smem, unsigned threads) {
-        return round_up(search_smem(n, c.wp, rows_smem, c.list), 16) + (size_t)(threads / 32) * t2w <= limit;
+        return round_up(search_smem(n, c.wp, rows_smem, c.list, c.local_slots), 16) + (size_t)(threads / 32) * t2w <=
+               limit;
     };
     c.smem = c.wp <= 32 && fits(true, c.threads);
     if (!c.smem && t2 && tu.t2_smem_rows && c.wp <= 32 && !o.threads_per_block) {
         // rows in shared memory with as many warps as fit beside them (one
         // warp at a time), with fewer lane-tier stack levels in shared memory
-        // when that buys warps (deeper levels go to local memory);
-        // G(1000, 0.3): 8 warps with four levels, 9 with three, 10 with two
+        // (deeper levels go to local memory) and then a half-size block ring
+        // when that buys warps; G(1000, 0.3): 8 warps with four levels, 9
+        // with three, 10 with two, 11 with one, 12 with one and 16 ring
+        // slots (6.2 -> 5.85 ms from 11 to 12)
         auto most = [&]() {
             unsigned th = c.threads;
             while (th >= 128 && !fits(true, th)) th -= 32;
             return th >= 128 ? th : 0u;
         };
         unsigned best = 0;
-        uint32_t best_levels = t2_levels;
-        for (uint32_t lv = t2_levels; lv >= 1; --lv) {
-            t2w = t2_warp_bytes(lv, o.pivot_mode != MCE_PIVOT_GREEDY);
-            const unsigned th = most();
-            if (th > best) {
-                best = th;
-                best_levels = lv;
+        uint32_t best_levels = t2_levels, best_slots = kLocalSlots;
+        for (uint32_t slots : {(uint32_t)kLocalSlots, (uint32_t)kLocalSlotsSmall}) {
+            c.local_slots = slots;
+            for (uint32_t lv = t2_levels; lv >= 1; --lv) {
+                t2w = t2_warp_bytes(lv, o.pivot_mode != MCE_PIVOT_GREEDY);
+                const unsigned th = most();
+                if (th > best) {
+                    best = th;
+                    best_levels = lv;
+                    best_slots = slots;
+                }
             }
         }
+        c.local_slots = best_slots;
         t2_levels = best_levels;
         t2w = t2_warp_bytes(t2_levels, o.pivot_mode != MCE_PIVOT_GREEDY);
         if (best) {
@@ -270,9 +279,9 @@ int choose(uint32_t n, const mce_options &o, Config &c, size_t stack_cap = ~(siz
         while (c.threads > 128 && !fits(c.smem, c.threads)) c.threads -= 64;
     const bool t2_on = t2 && fits(c.smem, c.threads);
     if (c.smem) c.impl = impl_for(G, K, true, (int)o.pivot_mode, c.list);
-    if (search_smem(n, c.wp, c.smem, c.list) > limit) return MCE_EINVAL;
+    if (search_smem(n, c.wp, c.smem, c.list, c.local_slots) > limit) return MCE_EINVAL;
 
-    size_t base = search_smem(n, c.wp, c.smem, c.list);
+    size_t base = search_smem(n, c.wp, c.smem, c.list, c.local_slots);
     if (t2_on) {
         c.t2_offset = (uint32_t)round_up(base, 16);
         c.t2_levels = t2_levels;
@@ -417,6 +426,7 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
     p.t2_levels = c.t2_levels;
     p.t2_max_p = c.t2_max_p;
     p.seed_children = c.seed ? 1u : 0u;
+    p.local_slots = c.local_slots;
     return p;
 }
 

@@ -33,8 +33,11 @@ struct Ctl {
 };
 
 // Per-block frame ring in shared memory (the first level of the work
-// distribution): header, kLocalSlots sequence numbers, kLocalSlots frames.
+// distribution): header, `slots` sequence numbers and `slots` frames, with
+// slots = kLocalSlots, or kLocalSlotsSmall where halving the ring buys a
+// warp of a plain search block (the planner decides).
 constexpr int kLocalSlots = 32;
+constexpr int kLocalSlotsSmall = 16;
 struct LocalHdr {
     unsigned head, tail;  // ring tickets
     unsigned idle;        // groups of this block without a frame
@@ -61,9 +64,9 @@ __host__ __device__ inline size_t frame_words(uint32_t wp, bool list = false)
 {
     return (8 + (list ? 3 : 2) * (size_t)wp + 3) / 4 * 4;
 }
-__host__ __device__ inline size_t local_queue_bytes(uint32_t wp, bool list = false)
+__host__ __device__ inline size_t local_queue_bytes(uint32_t wp, bool list = false, uint32_t slots = kLocalSlots)
 {
-    return sizeof(LocalHdr) + kLocalSlots * 4 + (size_t)kLocalSlots * frame_words(wp, list) * 4;
+    return sizeof(LocalHdr) + (size_t)slots * 4 + (size_t)slots * frame_words(wp, list) * 4;
 }
 
 // Clique listing (MCE_LIST).  Every group appends, at each maximal clique it
@@ -158,6 +161,7 @@ struct SearchParams {
     // start from the root's children, each its own queued frame, instead of
     // the root frame (the root is still counted once)
     uint32_t seed_children;
+    uint32_t local_slots;   // slots of the block ring (kLocalSlots or kLocalSlotsSmall)
 };
 
 // One graph of a batch (device table entry; pointers into library memory).
@@ -360,9 +364,10 @@ __host__ __device__ inline size_t smem_local_offset(uint32_t n, uint32_t wp, boo
     return smem_rows_bytes(n, wp, rows_in_smem) + (size_t)n * 8 +
            (((size_t)n + 1) * 4 + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false)
+__host__ __device__ inline size_t search_smem_bytes(uint32_t n, uint32_t wp, bool rows_in_smem, bool list = false,
+                                                   uint32_t slots = kLocalSlots)
 {
-    return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp, list);
+    return smem_local_offset(n, wp, rows_in_smem) + local_queue_bytes(wp, list, slots);
 }
 // Explicit-stack words per lane per level for groups of `lanes` lanes with
 // `words` words per lane: P, X and the level's scalars (one word when the

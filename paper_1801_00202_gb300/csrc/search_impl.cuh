@@ -408,11 +408,11 @@ __device__ __forceinline__ void load_row(uint32_t (&r)[K], const uint32_t *p)
 __device__ __forceinline__ unsigned vld(const unsigned *p) { return *reinterpret_cast<const volatile unsigned *>(p); }
 __device__ __forceinline__ void vst(unsigned *p, unsigned v) { *reinterpret_cast<volatile unsigned *>(p) = v; }
 
-__device__ __forceinline__ bool lq_reserve_push(LocalHdr *h, unsigned *seq, unsigned &ticket)
+__device__ __forceinline__ bool lq_reserve_push(LocalHdr *h, unsigned *seq, unsigned mask, unsigned &ticket)
 {
     unsigned pos = vld(&h->tail);
     for (unsigned t = 0; t < 256; ++t) {
-        const unsigned s = vld(&seq[pos & (kLocalSlots - 1)]);
+        const unsigned s = vld(&seq[pos & mask]);
         const int dif = (int)(s - pos);
         if (dif == 0) {
             const unsigned prev = atomicCAS(&h->tail, pos, pos + 1);
@@ -427,11 +427,11 @@ __device__ __forceinline__ bool lq_reserve_push(LocalHdr *h, unsigned *seq, unsi
     return false;
 }
 
-__device__ __forceinline__ bool lq_reserve_pop(LocalHdr *h, unsigned *seq, unsigned &ticket)
+__device__ __forceinline__ bool lq_reserve_pop(LocalHdr *h, unsigned *seq, unsigned mask, unsigned &ticket)
 {
     unsigned pos = vld(&h->head);
     for (unsigned t = 0; t < 256; ++t) {
-        const unsigned s = vld(&seq[pos & (kLocalSlots - 1)]);
+        const unsigned s = vld(&seq[pos & mask]);
         const int dif = (int)(s - (pos + 1));
         if (dif == 0) {
             const unsigned prev = atomicCAS(&h->head, pos, pos + 1);
@@ -450,14 +450,16 @@ struct LocalQ {
     LocalHdr *h;
     unsigned *seq;
     uint32_t *frames;
+    unsigned mask;  // slots - 1
 };
 
-__device__ __forceinline__ LocalQ local_queue_at(unsigned char *base, uint32_t wp)
+__device__ __forceinline__ LocalQ local_queue_at(unsigned char *base, uint32_t wp, uint32_t slots = kLocalSlots)
 {
     LocalQ q;
     q.h = reinterpret_cast<LocalHdr *>(base);
     q.seq = reinterpret_cast<unsigned *>(base + sizeof(LocalHdr));
-    q.frames = reinterpret_cast<uint32_t *>(base + sizeof(LocalHdr) + kLocalSlots * 4);
+    q.frames = reinterpret_cast<uint32_t *>(base + sizeof(LocalHdr) + (size_t)slots * 4);
+    q.mask = slots - 1u;
     (void)wp;
     return q;
 }
@@ -465,7 +467,7 @@ __device__ __forceinline__ LocalQ local_queue_at(unsigned char *base, uint32_t w
 // Reset the block's ring (whole block; a barrier must follow).
 __device__ __forceinline__ void local_queue_reset(const LocalQ &q, unsigned groups)
 {
-    for (unsigned i = threadIdx.x; i < (unsigned)kLocalSlots; i += blockDim.x) q.seq[i] = i;
+    for (unsigned i = threadIdx.x; i <= q.mask; i += blockDim.x) q.seq[i] = i;
     if (threadIdx.x == 0) {
         q.h->head = 0u;
         q.h->tail = 0u;
@@ -558,7 +560,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
     if (ok && g.leader()) {
         if (LOCAL) {
             atomicAdd(&lq.h->bwork, 1u);
-            got = lq_reserve_push(lq.h, lq.seq, ticket) ? 1u : 0u;
+            got = lq_reserve_push(lq.h, lq.seq, lq.mask, ticket) ? 1u : 0u;
             if (!got) atomicSub(&lq.h->bwork, 1u);
         } else {
             atomicAdd(&prm.ctl->pending, 1u);
@@ -574,7 +576,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
     for (int k = 0; k < K; ++k) l1[k] = got ? (L[k] & g.below(k, (unsigned)split)) : 0u;
     if (got) {
         if (LOCAL) {
-            volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * frame_words(WP, list);
+            volatile uint32_t *fr = lq.frames + (size_t)(ticket & lq.mask) * frame_words(WP, list);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 fr[kFrameHdr + g.gl * K + k] = P[k];
@@ -609,7 +611,7 @@ __device__ __forceinline__ bool donate_front(const Grp<G, K> &g, const SearchPar
     if (got && g.leader()) {
         if (LOCAL) {
             __threadfence_block();
-            vst(&lq.seq[ticket & (kLocalSlots - 1)], ticket + 1u);
+            vst(&lq.seq[ticket & lq.mask], ticket + 1u);
         } else {
             st_release(&prm.seq[ticket & (prm.qcap - 1u)], ticket + 1u);
         }
@@ -1408,12 +1410,12 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (busy_b == 0u && ld && !t2any) break;
             const unsigned lqueued = lt - lh;
             unsigned ticket = 0, got = 0;
-            if (!work && !held && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, ticket) ? 1u : 0u;
+            if (!work && !held && lqueued != 0u && g.leader()) got = lq_reserve_pop(lq.h, lq.seq, lq.mask, ticket) ? 1u : 0u;
             got = g.from_leader(got);
             ticket = g.from_leader(ticket);
             if (got) {
                 __threadfence_block();
-                const volatile uint32_t *fr = lq.frames + (size_t)(ticket & (kLocalSlots - 1)) * lfs;
+                const volatile uint32_t *fr = lq.frames + (size_t)(ticket & lq.mask) * lfs;
                 pe = fr[0];
                 rs = fr[1];
                 S = (uint64_t)fr[2] | ((uint64_t)fr[3] << 32);
@@ -1432,7 +1434,7 @@ __device__ __forceinline__ void search_loop(const SearchParams &prm, const uint3
             if (got) {
                 if (g.leader()) {
                     __threadfence_block();
-                    vst(&lq.seq[ticket & (kLocalSlots - 1)], ticket + kLocalSlots);
+                    vst(&lq.seq[ticket & lq.mask], ticket + lq.mask + 1u);
                     atomicSub(&lq.h->idle, 1u);
                     cn.note(kDiagSteals);
                 }
@@ -1901,7 +1903,7 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
     uint32_t *srows = reinterpret_cast<uint32_t *>(smem_raw);
     uint64_t *hv = reinterpret_cast<uint64_t *>(smem_raw + rbytes);
     uint32_t *hist = reinterpret_cast<uint32_t *>(hv + n);
-    const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP);
+    const LocalQ lq = local_queue_at(smem_raw + smem_local_offset(n, WP, SMEM), WP, prm.local_slots);
     local_queue_reset(lq, (blockDim.x / 32u) * (32u / G));
 
     // ---- prologue: stage the rows (bulk copy), hash terms, histogram
@@ -2164,6 +2166,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         prm.part_k = 0;
         prm.count_root = 1;
         prm.seed_children = 0;
+        prm.local_slots = kLocalSlots;
         prm.t2_offset = bp.t2_offset;
         prm.t2_levels = bp.t2_levels;
         prm.t2_max_p = bp.t2_max_p;
