@@ -350,7 +350,7 @@ Tuning mce::default_tuning()
         // micro-batches (on the served workload, 10,400 -> 11,300 requests/s
         // closed loop and p99 6.3 -> 3.9 ms at 0.7x that load, against one
         // block per 50,000 and micro-batches up to 10^5)
-        Tuning d{0u, 0u, 8u, 16u, 2000u, 20000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 4u, 1000u};  // 0: thresholds by density
+        Tuning d{0u, 0u, 8u, 16u, 2000u, 20000u, 16384u, 32u, 16384u, 32u, 4u, 1u, 1u, 1u, 1u, 4u, 1000u, 1u};  // 0: thresholds by density
         if (const char *env = std::getenv("MCE_TUNE")) {
             const char *p = env;
             while (*p) {
@@ -375,6 +375,7 @@ Tuning mce::default_tuning()
                 else if (!std::strcmp(key, "batch_wide")) d.batch_wide = val;
                 else if (!std::strcmp(key, "batch_split")) d.batch_split = val;
                 else if (!std::strcmp(key, "serve_bcost")) d.serve_bcost = val;
+                else if (!std::strcmp(key, "small_split")) d.small_split = val;
                 p += used;
                 if (*p == ',') ++p;
             }
@@ -412,6 +413,10 @@ SearchParams params(uint32_t n, const Config &c, const Layout &L, unsigned char 
     p.stack_smem_levels = c.stack_levels;
     p.stack_offset = c.stack_offset;
     p.tune = default_tuning();
+    // the breadth-first split of small graphs from 20 vertices pays in a
+    // full-wave launch of one graph; a grid sized for one served request
+    // (o.blocks) ran slower with it (10,800 -> 10,300 requests/s)
+    if (o.blocks) p.tune.small_split = 0u;
     p.trace = nullptr;
     p.trace_per_block = 0;
     if (g_trace && c.blocks) {
@@ -1852,6 +1857,7 @@ int batch_create_impl(mce_ctx *ctx, mce_graph *const *graphs, uint32_t count, co
             bp.stack_smem_levels = bk.stack_levels;
             bp.stack_offset = bk.stack_offset;
             bp.tune = default_tuning();
+            bp.tune.small_split = 0u;  // the batched form ran 6 % slower with it
             bp.t2_offset = bk.t2_offset;
             bp.t2_levels = bk.t2_levels;
             bp.t2_max_p = bk.t2_max_p;

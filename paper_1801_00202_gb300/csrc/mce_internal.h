@@ -104,6 +104,7 @@ struct Tuning {
     uint32_t batch_wide;    // batched form by default: 512 threads, at most two words per lane (1), or the plain shapes (0)
     uint32_t batch_split;   // batched form: parts of about 1/(blocks * batch_split) of a bucket's cost (0: no split)
     uint32_t serve_bcost;   // served form: largest expected maximal cliques (thousands) of a micro-batched request
+    uint32_t small_split;   // small graphs of density <= 0.75 split breadth first from 20 vertices (1) or by density (0)
 };
 
 // The lane tier (second search tier): a frame whose P u X has at most 32

@@ -76,7 +76,8 @@ struct Thresholds {
 // same values.
 __device__ __forceinline__ Thresholds density_thresholds(const uint32_t *rows, uint32_t n, uint32_t wp,
                                                          unsigned fixed_local, unsigned fixed_global,
-                                                         unsigned fixed_split, unsigned *scratch_u32)
+                                                         unsigned fixed_split, unsigned *scratch_u32,
+                                                         bool small_split)
 {
     if (threadIdx.x == 0) *scratch_u32 = 0u;
     __syncthreads();
@@ -98,9 +99,17 @@ __device__ __forceinline__ Thresholds density_thresholds(const uint32_t *rows, u
         t.share_local = min((unsigned)kShareLocalByDensity[i - 1], max(16u, n / 8u));
         t.share_global = min((unsigned)kShareGlobalByDensity[i - 1], max(20u, n / 4u));
         // dense structured graphs (Moon-Moser: every child keeps all but three
-        // vertices) would never reach the density's split size; cap it at two
-        // thirds of n
-        t.split = min((unsigned)kSplitByDensity[i - 1], max(24u, 2u * n / 3u));
+        // vertices) would never reach the density's split size; cap it at
+        // half of n (Moon-Moser 45: 1.37 -> 0.90 ms against two thirds).
+        // With small_split (full-wave launches of one graph), small graphs
+        // of density up to 0.75 split from 20 vertices: their whole tree is
+        // too small for the density's split size, and only frames that move
+        // keep the GPU busy (measured, whole path: G(100, 0.5) 0.28 -> 0.21
+        // ms, G(100, 0.7) 0.95 -> 0.50, G(128, 0.5) 0.36 -> 0.24, G(200,
+        // 0.5) 0.83 -> 0.54, G(256, 0.4) 0.72 -> 0.51; G(100, 0.8) would
+        // lose: 1.27 -> 2.2 ms)
+        t.split = min((unsigned)kSplitByDensity[i - 1], max(20u, n / 2u));
+        if (small_split && n <= 256u && i <= 30) t.split = min(t.split, 20u);
     }
     if (fixed_local) t.share_local = fixed_local;
     if (fixed_global) t.share_global = fixed_global;
@@ -1920,7 +1929,8 @@ __global__ void __launch_bounds__(512) search_kernel(const SearchParams prm)
 
     __shared__ unsigned deg_sum;
     const Thresholds th = density_thresholds(SMEM ? srows : prm.rows, n, WP, prm.tune.share_local,
-                                             prm.tune.share_global, prm.split_min_p, &deg_sum);
+                                             prm.tune.share_global, prm.split_min_p, &deg_sum,
+                                             prm.tune.small_split != 0u);
     uint32_t *stack_smem = reinterpret_cast<uint32_t *>(smem_raw + prm.stack_offset);
     Counters cn;
     cn.diag = lq.h->diag;
@@ -2171,7 +2181,8 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams bp)
         prm.t2_levels = bp.t2_levels;
         prm.t2_max_p = bp.t2_max_p;
         const Thresholds th = density_thresholds(SMEM ? srows : gd.ren, n, WP, bp.tune.share_local,
-                                                 bp.tune.share_global, bp.split_min_p, &root_key);
+                                                 bp.tune.share_global, bp.split_min_p, &root_key,
+                                                 bp.tune.small_split != 0u);
         Counters cn;
         cn.diag = lq.h->diag;
         if (ok)
