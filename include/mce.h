@@ -251,9 +251,8 @@ int mce_enumerate_device(uint32_t n, uint32_t words_per_row, const uint32_t *d_r
  * that must not allocate per call.  The caller still owns d_rows and d_out.
  *  - Every call looks up the area's device address (cudaGetSymbolAddress,
  *    with the calling thread's current device); the first call on a device
- *    loads the library's device code there, so make it before any stream
- *    capture.  A device reset invalidates nothing kept by the library: the
- *    next call looks the area up again.
+ *    loads the library's device code there.  A device reset invalidates
+ *    nothing kept by the library: the next call looks the area up again.
  *  - Every call reuses the same area; what must start from a known state is
  *    re-initialised by each call, but calls whose work overlaps on the GPU
  *    race on the area: do not issue overlapping calls (other streams, other

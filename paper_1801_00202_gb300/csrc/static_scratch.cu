@@ -14,8 +14,8 @@
 // cudaGetSymbolAddress, with the device current, on every call: a device
 // reset, or a primary context released and created again, reloads the module
 // and may move the area, so no address is kept between calls.  The first
-// call on a device loads the module there; make it before any stream
-// capture.  Every call uses the same area and the search re-initialises all
+// call on a device loads the module there.  Every call uses the same area
+// and the search re-initialises all
 // of it that must start from zero or a known state (queue tickets, control
 // counters, root frame; the caller's d_out is zeroed by the search too), but
 // two calls whose work overlaps on the GPU -- on different streams, or on one
